@@ -1,0 +1,197 @@
+/*
+ * hisq.h -- C ABI of the GB300 (sm_103a) HISQ even/odd staggered operator library.
+ *
+ * The library applies the even/odd halves D_eo / D_oe of the HISQ staggered Dirac
+ * operator and solves with A = M^dag M = 4 m^2 - D_eo D_oe by CG (plain FP64, mixed
+ * precision with FP64 reliable updates, several right-hand sides) and multi-shift CG.
+ * These are the operations the paper singles out: "applying the Dslash operator to a
+ * vector" is "the most performance-critical kernel" of the CG that takes about 60% of
+ * HISQ RHMC time, and the CG comes in multi-RHS, multi-shift and mixed-precision forms
+ * (Sec. 3 and the module list of Sec. 2).
+ *
+ * Conventions (the paper writes no formula; these are the textbook HISQ ones):
+ *   lattice    dims = {Lx, Ly, Lz, Lt}, each even and >= 4; periodic index wrap.
+ *   site       idx = x + Lx*(y + Ly*(z + Lz*t)); parity = (x+y+z+t) mod 2, even = 0;
+ *              cb = idx / 2 numbers the V/2 sites of one parity.
+ *   operator   (D chi)(x) = sum_mu [ F_mu(x) chi(x+mu) - F_mu(x-mu)^dag chi(x-mu)
+ *                                  + L_mu(x) chi(x+3mu) - L_mu(x-3mu)^dag chi(x-3mu) ]
+ *              F = fat links, L = long (Naik) links with the Naik coefficient already
+ *              included; staggered phases eta_mu(x) = (-1)^(x_0+..+x_{mu-1}) and the
+ *              antiperiodic-t sign are folded in at load time (flags below). No factor
+ *              1/2, so M = 2m + D and M^dag M on even sites is 4m^2 - D_eo D_oe.
+ *              D_eo maps odd-site vectors to even sites; D_oe maps even to odd.
+ *
+ * Data at the boundary:
+ *   links      host, complex128 interleaved (re, im), [t][z][y][x][mu][row][col],
+ *              x fastest, mu = 0..3 = x, y, z, t.
+ *   vectors    [rhs][cb][color] over the sites of one parity, complex numbers stored
+ *              as (re, im) pairs of the precision's real type: HISQ_F64 complex128,
+ *              HISQ_F32 complex64, HISQ_F16 two IEEE binary16, HISQ_BF16 two bfloat16.
+ *              Solver vectors are always complex128. A vector argument may point to
+ *              device memory or to host memory (pageable or pinned); host data is
+ *              staged through library-owned device buffers on the context's stream.
+ *
+ * Ownership and threading: the context owns its link storage and its device
+ * workspaces; the caller owns every array it passes. One context serves one CUDA
+ * stream; calls on one context must not run concurrently from several threads.
+ * All work is issued on the context's stream; entry points that return results
+ * to the host (solvers, host output vectors) synchronise that stream before they
+ * return.
+ *
+ * Errors: every entry point returns HISQ_OK (0) or a negative HISQ_E* code and never
+ * aborts, traps or prints. hisq_strerror() names a code; hisq_last_error() gives the
+ * detail of the most recent failure in the calling thread.
+ */
+#ifndef HISQ_H
+#define HISQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+  HISQ_OK = 0,
+  HISQ_EINVAL = -1,      /* bad argument: dims, parity, null pointer, nrhs, precision not resident */
+  HISQ_ENOLINKS = -2,    /* links not (fully) loaded */
+  HISQ_ENOMEM = -3,      /* device or host allocation failed */
+  HISQ_ECUDA = -4,       /* a CUDA runtime call failed; hisq_last_error() has its text */
+  HISQ_ENONFINITE = -5,  /* NaN or Inf in links, source or an intermediate reduction */
+  HISQ_ENOCONV = -6,     /* maxiter reached; x holds the last iterate, stats the true residual */
+  HISQ_EBREAKDOWN = -7,  /* CG breakdown: <p, A p> <= 0 */
+  HISQ_ETIMEOUT = -8     /* a bounded device-side wait ran out */
+};
+
+/* ---------------------------------------------------------------- precisions */
+typedef enum { HISQ_F64 = 0, HISQ_F32 = 1, HISQ_F16 = 2, HISQ_BF16 = 3 } hisq_prec;
+#define HISQ_PREC_BIT(p) (1u << (unsigned)(p))
+#define HISQ_PREC_ALL 0xFu
+
+/* ---------------------------------------------------------------- link-load flags */
+#define HISQ_APPLY_PHASES 1u   /* multiply eta_mu(x) into fat and long links */
+#define HISQ_ANTIPERIODIC_T 2u /* negate F_t at t = Lt-1 and L_t at t >= Lt-3 */
+
+typedef struct hisq_ctx hisq_ctx;
+
+/*
+ * Create a context for one lattice. dims: {Lx, Ly, Lz, Lt}, each even and >= 4.
+ * prec_mask: OR of HISQ_PREC_BIT(p) for every storage precision whose links should
+ * be kept resident (HISQ_F64 is always added: reliable updates and true residuals
+ * need it). stream: a cudaStream_t (NULL = legacy default stream), borrowed.
+ * Allocates the link storage: 8 links x 18 reals x V per resident precision.
+ * Errors: HISQ_EINVAL, HISQ_ENOMEM, HISQ_ECUDA.
+ */
+int hisq_create(hisq_ctx** out, const int dims[4], unsigned prec_mask, void* stream);
+
+/* Free every device and host resource of the context. NULL is accepted. */
+int hisq_destroy(hisq_ctx* ctx);
+
+/*
+ * Load fat and long links for the whole lattice (host arrays in the link layout
+ * above, V*4*9 complex128 each). flags: HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T.
+ * The links are folded (phases, boundary sign) and converted to every resident
+ * precision on the device; the host arrays are not kept. Returns HISQ_ENONFINITE if
+ * any entry is NaN or Inf (the previous links are then no longer valid).
+ */
+int hisq_load_links(hisq_ctx* ctx, const double* fat, const double* lng, unsigned flags);
+
+/*
+ * Load the links of the t-slices [t_begin, t_begin + t_count) only; fat and lng then
+ * hold t_count*Lz*Ly*Lx*4*9 complex128 each. Lets lattices whose host link arrays would
+ * not fit in host memory be loaded slab by slab. The context is ready once every
+ * t-slice has been loaded (with the same flags).
+ */
+int hisq_load_links_slab(hisq_ctx* ctx, int t_begin, int t_count, const double* fat, const double* lng,
+                         unsigned flags);
+
+/*
+ * out = D_eo in (out_parity = 0: out on even sites, in on odd sites), or
+ * out = D_oe in (out_parity = 1). Vectors in precision prec (its links must be
+ * resident), nrhs vectors of V/2 sites back to back; out and in must not overlap.
+ * Arithmetic: FP64 for HISQ_F64, FP32 for the others (16-bit types are storage only).
+ * Asynchronous on the context's stream for device pointers.
+ * Errors: HISQ_EINVAL (parity, nrhs < 1 or > 64, precision not resident), HISQ_ENOLINKS.
+ */
+int hisq_dslash(hisq_ctx* ctx, int out_parity, void* out, const void* in, int prec, int nrhs);
+
+/*
+ * out = (4 m^2 + sigma) in - D_eo D_oe in on even sites (the operator CG inverts,
+ * shifted by sigma). Same vector conventions as hisq_dslash.
+ */
+int hisq_apply_A(hisq_ctx* ctx, void* out, const void* in, double mass, double sigma, int prec, int nrhs);
+
+/* ---------------------------------------------------------------- solvers */
+typedef struct {
+  int inner_prec;       /* HISQ_F64: plain FP64 CG. HISQ_F32 / F16 / BF16: mixed precision --
+                           inner CG with links in that precision, FP32 spinors and arithmetic,
+                           FP64 reductions and FP64 solution accumulator, FP64 reliable updates */
+  int reliable_period;  /* inner iterations between FP64 reliable updates (default 50) */
+  int use_graph;        /* 1: capture blocks of iterations in a CUDA graph (default 1) */
+  int poll_every;       /* iterations between host convergence polls (default 25) */
+} hisq_solver_opts;
+
+typedef struct {
+  int iters;                  /* CG iterations (inner iterations for mixed precision) */
+  int reliable_updates;       /* FP64 residual recomputations */
+  int converged;              /* 1 if every rhs / shift met its tolerance */
+  double true_rel_residual;   /* max over rhs / shifts of ||b - (A+sigma) x|| / ||b||, FP64, at exit */
+  double seconds;             /* wall time of the solve inside the library */
+  double dslash_bytes;        /* algorithmic bytes of all Dslash applications in the solve */
+  long long dslash_calls;     /* Dslash applications (one rhs-block counts once) */
+  int shift_iters[64];        /* multi-shift: iteration at which each shift converged */
+  double shift_residual[64];  /* true residual of each shift (multi-shift) or rhs (CG) */
+  long long kernel_launches;  /* CUDA kernels this call executed (graph nodes included) */
+} hisq_solver_stats;
+
+/* Fill opts with the defaults above (inner_prec = HISQ_F64). */
+void hisq_solver_opts_default(hisq_solver_opts* opts);
+
+/*
+ * Solve A x_r = b_r (A = 4 m^2 - D_eo D_oe) for nrhs right-hand sides at once, each to
+ * ||b_r - A x_r|| <= rel_tol ||b_r||, judged by the true FP64 residual at exit.
+ * x: complex128 [nrhs][V/2][3], the initial guess on entry (zero is fine) and the
+ * solution on exit; b: the sources, same layout. Host or device pointers.
+ * opts may be NULL (defaults); stats may be NULL.
+ * Errors: HISQ_EINVAL (mass <= 0, rel_tol <= 0, nrhs out of range, inner precision not
+ * resident), HISQ_ENOLINKS, HISQ_ENONFINITE, HISQ_ENOCONV, HISQ_EBREAKDOWN, HISQ_ECUDA.
+ */
+int hisq_cg(hisq_ctx* ctx, double* x, const double* b, int nrhs, double mass, double rel_tol, int maxiter,
+            const hisq_solver_opts* opts, hisq_solver_stats* stats);
+
+/*
+ * Multi-shift CG: (A + sigma_k) x_k = b for nshift shifts sigma_k >= 0 from one Krylov
+ * space (the RHMC use of the CG, Sec. 2 and Sec. 3). x: nshift complex128 vectors
+ * [nshift][V/2][3] (output; initial contents ignored); b: one source. rel_tol: nshift
+ * tolerances. With opts->inner_prec != HISQ_F64 the shared Krylov space is built in
+ * that precision (FP64 reductions and accumulators) and each shift is then refined
+ * by mixed-precision CG with FP64 reliable updates until its true residual meets
+ * its tolerance. nshift <= 64.
+ */
+int hisq_multishift_cg(hisq_ctx* ctx, double* x, const double* b, int nshift, const double* shifts,
+                       double mass, const double* rel_tol, int maxiter, const hisq_solver_opts* opts,
+                       hisq_solver_stats* stats);
+
+/* ---------------------------------------------------------------- diagnostics */
+const char* hisq_strerror(int code);
+const char* hisq_last_error(void);
+
+/* Algorithmic bytes of one Dslash application on one parity in precision prec with
+ * nrhs vectors: (V/2) * (16 links * 18 + nrhs * (6 in + 6 out)) reals. */
+double hisq_dslash_bytes(const hisq_ctx* ctx, int prec, int nrhs);
+
+/* Number of CUDA kernels this context has executed so far (eager launches, autotuning
+ * trials and every node of every graph launch). */
+long long hisq_launch_count(const hisq_ctx* ctx);
+
+/* Autotuner: choose launch shapes by timing (default on). The cache lives in the
+ * context; hisq_tune_report writes "kernel dims prec nrhs -> block" lines to buf. */
+int hisq_set_autotune(hisq_ctx* ctx, int enable);
+int hisq_tune_report(const hisq_ctx* ctx, char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HISQ_H */

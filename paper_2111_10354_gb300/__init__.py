@@ -1,0 +1,279 @@
+"""Python binding of the GB300 HISQ even/odd operator library (libhisq.so).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA kernels.
+The functions carry the C ABI's names (include/hisq.h). Vectors may be torch tensors (device
+or host) or numpy arrays; they are passed to the library as raw pointers.
+
+If libhisq.so has not been built, every call raises RuntimeError: there is no CPU fallback.
+Build it with ``paper_2111_10354_gb300.build.build()`` (needs nvcc) or ``__graft_entry__.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhisq.so")
+
+HISQ_OK = 0
+HISQ_EINVAL = -1
+HISQ_ENOLINKS = -2
+HISQ_ENOMEM = -3
+HISQ_ECUDA = -4
+HISQ_ENONFINITE = -5
+HISQ_ENOCONV = -6
+HISQ_EBREAKDOWN = -7
+HISQ_ETIMEOUT = -8
+
+HISQ_F64, HISQ_F32, HISQ_F16, HISQ_BF16 = 0, 1, 2, 3
+PREC_NAMES = {HISQ_F64: "f64", HISQ_F32: "f32", HISQ_F16: "f16", HISQ_BF16: "bf16"}
+HISQ_APPLY_PHASES = 1
+HISQ_ANTIPERIODIC_T = 2
+HISQ_PREC_ALL = 0xF
+
+
+def HISQ_PREC_BIT(p: int) -> int:
+    return 1 << p
+
+
+class hisq_solver_opts(ctypes.Structure):
+    _fields_ = [("inner_prec", ctypes.c_int), ("reliable_period", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("poll_every", ctypes.c_int)]
+
+
+class hisq_solver_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("converged", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("dslash_bytes", ctypes.c_double), ("dslash_calls", ctypes.c_longlong),
+                ("shift_iters", ctypes.c_int * 64), ("shift_residual", ctypes.c_double * 64),
+                ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("shift_iters", "shift_residual")}
+        return d
+
+
+class HisqError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str, stats=None):
+        self.code = code
+        self.stats = stats
+        super().__init__("%s: %s (%d): %s" % (where, hisq_strerror(code), code, detail))
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libhisq.so is not built (%s); run paper_2111_10354_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.hisq_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.c_uint, vp]
+    lib.hisq_destroy.argtypes = [vp]
+    lib.hisq_load_links.argtypes = [vp, vp, vp, ctypes.c_uint]
+    lib.hisq_load_links_slab.argtypes = [vp, ip, ip, vp, vp, ctypes.c_uint]
+    lib.hisq_dslash.argtypes = [vp, ip, vp, vp, ip, ip]
+    lib.hisq_apply_A.argtypes = [vp, vp, vp, dp, dp, ip, ip]
+    lib.hisq_solver_opts_default.argtypes = [ctypes.POINTER(hisq_solver_opts)]
+    lib.hisq_solver_opts_default.restype = None
+    lib.hisq_cg.argtypes = [vp, vp, vp, ip, dp, dp, ip, ctypes.POINTER(hisq_solver_opts),
+                            ctypes.POINTER(hisq_solver_stats)]
+    if hasattr(lib, "hisq_multishift_cg"):
+        lib.hisq_multishift_cg.argtypes = [vp, vp, vp, ip, vp, dp, vp, ip, ctypes.POINTER(hisq_solver_opts),
+                                           ctypes.POINTER(hisq_solver_stats)]
+    lib.hisq_strerror.argtypes = [ip]
+    lib.hisq_strerror.restype = ctypes.c_char_p
+    lib.hisq_last_error.argtypes = []
+    lib.hisq_last_error.restype = ctypes.c_char_p
+    lib.hisq_dslash_bytes.argtypes = [vp, ip, ip]
+    lib.hisq_dslash_bytes.restype = ctypes.c_double
+    lib.hisq_set_autotune.argtypes = [vp, ip]
+    lib.hisq_launch_count.argtypes = [vp]
+    lib.hisq_launch_count.restype = ctypes.c_longlong
+    lib.hisq_tune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    _lib = lib
+    return lib
+
+
+def lib():
+    return _load()
+
+
+def _check(rc: int, where: str, stats=None):
+    if rc != HISQ_OK:
+        raise HisqError(rc, where, hisq_last_error(), stats)
+
+
+def _ptr(a):
+    """Raw pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    raise TypeError("expected a torch tensor, numpy array or pointer, got %r" % type(a))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream) if stream.cuda_stream else None
+    return ctypes.c_void_p(int(stream))
+
+
+# ---------------------------------------------------------------- C ABI, same names
+
+def hisq_strerror(code: int) -> str:
+    return _load().hisq_strerror(code).decode()
+
+
+def hisq_last_error() -> str:
+    return _load().hisq_last_error().decode()
+
+
+def hisq_create(dims, prec_mask: int = HISQ_PREC_ALL, stream=None):
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(_load().hisq_create(ctypes.byref(h), d, prec_mask, _stream_handle(stream)), "hisq_create")
+    return h
+
+
+def hisq_destroy(ctx):
+    _check(_load().hisq_destroy(ctx), "hisq_destroy")
+
+
+def hisq_load_links(ctx, fat, lng, flags: int = HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T):
+    fat = np.ascontiguousarray(fat, dtype=np.complex128)
+    lng = np.ascontiguousarray(lng, dtype=np.complex128)
+    _check(_load().hisq_load_links(ctx, _ptr(fat), _ptr(lng), flags), "hisq_load_links")
+
+
+def hisq_load_links_slab(ctx, t_begin: int, t_count: int, fat, lng,
+                         flags: int = HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T):
+    fat = np.ascontiguousarray(fat, dtype=np.complex128)
+    lng = np.ascontiguousarray(lng, dtype=np.complex128)
+    _check(_load().hisq_load_links_slab(ctx, t_begin, t_count, _ptr(fat), _ptr(lng), flags), "hisq_load_links_slab")
+
+
+def hisq_dslash(ctx, out_parity: int, out, in_, prec: int, nrhs: int = 1):
+    _check(_load().hisq_dslash(ctx, out_parity, _ptr(out), _ptr(in_), prec, nrhs), "hisq_dslash")
+
+
+def hisq_apply_A(ctx, out, in_, mass: float, sigma: float, prec: int, nrhs: int = 1):
+    _check(_load().hisq_apply_A(ctx, _ptr(out), _ptr(in_), mass, sigma, prec, nrhs), "hisq_apply_A")
+
+
+def hisq_solver_opts_default() -> hisq_solver_opts:
+    o = hisq_solver_opts()
+    _load().hisq_solver_opts_default(ctypes.byref(o))
+    return o
+
+
+def make_opts(inner_prec: int = HISQ_F64, reliable_period: int = 50, use_graph: bool = True, poll_every: int = 25):
+    o = hisq_solver_opts_default()
+    o.inner_prec, o.reliable_period, o.use_graph, o.poll_every = inner_prec, reliable_period, int(use_graph), \
+        poll_every
+    return o
+
+
+def hisq_cg(ctx, x, b, nrhs: int, mass: float, rel_tol: float, maxiter: int, opts=None, raise_on_error=True):
+    """Returns (status, stats dict). x is updated in place."""
+    st = hisq_solver_stats()
+    o = opts if opts is not None else hisq_solver_opts_default()
+    rc = _load().hisq_cg(ctx, _ptr(x), _ptr(b), nrhs, mass, rel_tol, maxiter, ctypes.byref(o), ctypes.byref(st))
+    d = st.as_dict()
+    if rc != HISQ_OK and raise_on_error:
+        raise HisqError(rc, "hisq_cg", hisq_last_error(), d)
+    return rc, d
+
+
+def hisq_multishift_cg(ctx, x, b, shifts, mass: float, rel_tol, maxiter: int, opts=None, raise_on_error=True):
+    """x: nshift vectors back to back. Returns (status, stats dict with per-shift lists)."""
+    shifts = np.ascontiguousarray(shifts, dtype=np.float64)
+    ns = len(shifts)
+    tols = np.ascontiguousarray(np.broadcast_to(np.asarray(rel_tol, np.float64), (ns,)))
+    st = hisq_solver_stats()
+    o = opts if opts is not None else hisq_solver_opts_default()
+    rc = _load().hisq_multishift_cg(ctx, _ptr(x), _ptr(b), ns, _ptr(shifts), mass, _ptr(tols), maxiter,
+                                    ctypes.byref(o), ctypes.byref(st))
+    d = st.as_dict()
+    d["shift_iters"] = [int(st.shift_iters[k]) for k in range(ns)]
+    d["shift_residual"] = [float(st.shift_residual[k]) for k in range(ns)]
+    if rc != HISQ_OK and raise_on_error:
+        raise HisqError(rc, "hisq_multishift_cg", hisq_last_error(), d)
+    return rc, d
+
+
+def hisq_dslash_bytes(ctx, prec: int, nrhs: int = 1) -> float:
+    return float(_load().hisq_dslash_bytes(ctx, prec, nrhs))
+
+
+def hisq_launch_count(ctx) -> int:
+    return int(_load().hisq_launch_count(ctx))
+
+
+def hisq_set_autotune(ctx, enable: bool):
+    _check(_load().hisq_set_autotune(ctx, int(enable)), "hisq_set_autotune")
+
+
+def hisq_tune_report(ctx) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(_load().hisq_tune_report(ctx, buf, len(buf)), "hisq_tune_report")
+    return buf.value.decode()
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+class Lattice:
+    """Owns one context: ``Lattice(dims).load(fat, lng)`` then ``dslash`` / ``cg``."""
+
+    def __init__(self, dims, precs=(HISQ_F64, HISQ_F32, HISQ_F16, HISQ_BF16), stream=None):
+        mask = 0
+        for p in precs:
+            mask |= HISQ_PREC_BIT(p)
+        self.dims = tuple(int(v) for v in dims)
+        self.half = int(np.prod(self.dims)) // 2
+        self.ctx = hisq_create(self.dims, mask, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            hisq_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, fat, lng, flags=HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T):
+        hisq_load_links(self.ctx, fat, lng, flags)
+        return self
+
+    def dslash(self, out_parity, out, in_, prec, nrhs=1):
+        hisq_dslash(self.ctx, out_parity, out, in_, prec, nrhs)
+
+    def apply_A(self, out, in_, mass, prec, nrhs=1, sigma=0.0):
+        hisq_apply_A(self.ctx, out, in_, mass, sigma, prec, nrhs)
+
+    def cg(self, x, b, mass, rel_tol=1e-10, maxiter=10000, nrhs=1, **opts):
+        return hisq_cg(self.ctx, x, b, nrhs, mass, rel_tol, maxiter, make_opts(**opts))
+
+    def multishift_cg(self, x, b, shifts, mass, rel_tol=1e-9, maxiter=10000, **opts):
+        return hisq_multishift_cg(self.ctx, x, b, shifts, mass, rel_tol, maxiter, make_opts(**opts))
+
+    def dslash_bytes(self, prec, nrhs=1):
+        return hisq_dslash_bytes(self.ctx, prec, nrhs)

@@ -1,0 +1,405 @@
+// C ABI: context life cycle, link loading (fold + pack), Dslash and A dispatch, staging
+// of host vectors, errors.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "internal.cuh"
+#include "tune.h"
+
+namespace hisq {
+
+int dslash_launch_f64(hisq_ctx* ctx, int sp, const DslashCall& c);
+int dslash_launch_f32(hisq_ctx* ctx, int sp, const DslashCall& c);
+int dslash_launch_f16(hisq_ctx* ctx, int sp, const DslashCall& c);
+int dslash_launch_bf16(hisq_ctx* ctx, int sp, const DslashCall& c);
+
+static thread_local char g_last_error[512] = "";
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  set_error(HISQ_ECUDA, "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+  return e == cudaErrorMemoryAllocation ? HISQ_ENOMEM : HISQ_ECUDA;
+}
+
+void* workspace(hisq_ctx* ctx, const char* name, size_t bytes) {
+  DevBuf& b = ctx->ws[name];
+  if (b.bytes >= bytes && b.ptr) return b.ptr;
+  if (b.ptr) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.ptr = nullptr;
+    return nullptr;
+  }
+  b.bytes = bytes;
+  return b.ptr;
+}
+
+int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
+  if (!ctx->links[lp]) return set_error(HISQ_EINVAL, "link precision %d is not resident", lp);
+  switch (lp) {
+    case HISQ_F64: return dslash_launch_f64(ctx, sp, c);
+    case HISQ_F32: return dslash_launch_f32(ctx, sp, c);
+    case HISQ_F16: return dslash_launch_f16(ctx, sp, c);
+    case HISQ_BF16: return dslash_launch_bf16(ctx, sp, c);
+  }
+  return set_error(HISQ_EINVAL, "bad precision %d", lp);
+}
+
+double dslash_bytes(const hisq_ctx* ctx, int lp, int sp, int nrhs) {
+  // algorithmic: every link once, every vector read once and written once
+  return (double)ctx->g.half * (16.0 * 18.0 * real_size(lp) + nrhs * 12.0 * real_size(sp));
+}
+
+// ------------------------------------------------------------------ link packing (fold)
+// One thread per site of the slab: multiply eta_mu(x) (HISQ_APPLY_PHASES) and the
+// antiperiodic-t sign (fat at t = Lt-1, long at t >= Lt-3), then store the link in the
+// chunk-plane layout of every resident precision. Non-finite entries raise *bad.
+__global__ void pack_links_kernel(Geom g, const double2* __restrict__ fat, const double2* __restrict__ lng, int t0,
+                                  int nt, unsigned flags, char* l64, char* l32, char* l16, char* lbf, int* bad) {
+  const int slab = g.L[0] * g.L[1] * g.L[2];
+  const int n = slab * nt;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    int c[4];
+    c[0] = s % g.L[0];
+    c[1] = (s / g.L[0]) % g.L[1];
+    c[2] = (s / (g.L[0] * g.L[1])) % g.L[2];
+    c[3] = t0 + s / slab;
+    const int idx = lex_index(g, c);
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    const int cb = idx >> 1;
+    for (int kind = 0; kind < 2; ++kind) {
+      const double2* src = kind == 0 ? fat : lng;
+      for (int mu = 0; mu < 4; ++mu) {
+        double sign = 1.0;
+        if (flags & HISQ_APPLY_PHASES) {
+          int sum = 0;
+          for (int nu = 0; nu < mu; ++nu) sum += c[nu];
+          if (sum & 1) sign = -sign;
+        }
+        if ((flags & HISQ_ANTIPERIODIC_T) && mu == 3) {
+          if (kind == 0 && c[3] == g.L[3] - 1) sign = -sign;
+          if (kind == 1 && c[3] >= g.L[3] - 3) sign = -sign;
+        }
+        cplx<double> U[9];
+        bool finite = true;
+        for (int k = 0; k < 9; ++k) {
+          double2 v = src[((size_t)s * 4 + mu) * 9 + k];
+          finite = finite && isfinite(v.x) && isfinite(v.y);
+          U[k] = {sign * v.x, sign * v.y};
+        }
+        if (!finite) atomicOr(bad, 1);
+        const size_t blk = (size_t)((par * 2 + kind) * 4 + mu);
+        if (l64) LinkIO<double>::store(l64 + blk * link_block_bytes(HISQ_F64, g.half), g.half, cb, U);
+        if (l32) LinkIO<float>::store(l32 + blk * link_block_bytes(HISQ_F32, g.half), g.half, cb, U);
+        if (l16) LinkIO<__half>::store(l16 + blk * link_block_bytes(HISQ_F16, g.half), g.half, cb, U);
+        if (lbf) LinkIO<__nv_bfloat16>::store(lbf + blk * link_block_bytes(HISQ_BF16, g.half), g.half, cb, U);
+      }
+    }
+  }
+}
+
+int pack_links_slab(hisq_ctx* ctx, const double* d_fat, const double* d_long, int t0, int nt, unsigned flags) {
+  const int n = ctx->g.L[0] * ctx->g.L[1] * ctx->g.L[2] * nt;
+  const int block = 128;
+  int grid = (n + block - 1) / block;
+  if (grid > ctx->num_sms * 32) grid = ctx->num_sms * 32;
+  pack_links_kernel<<<grid, block, 0, ctx->stream>>>(ctx->g, (const double2*)d_fat, (const double2*)d_long, t0, nt,
+                                                     flags, ctx->links[0], ctx->links[1], ctx->links[2],
+                                                     ctx->links[3], ctx->d_flag);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx);
+  return HISQ_OK;
+}
+
+// ------------------------------------------------------------------ vector staging
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace hisq
+
+using namespace hisq;
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* hisq_strerror(int code) {
+  switch (code) {
+    case HISQ_OK: return "success";
+    case HISQ_EINVAL: return "invalid argument";
+    case HISQ_ENOLINKS: return "links not loaded";
+    case HISQ_ENOMEM: return "out of memory";
+    case HISQ_ECUDA: return "CUDA error";
+    case HISQ_ENONFINITE: return "non-finite value";
+    case HISQ_ENOCONV: return "solver did not converge";
+    case HISQ_EBREAKDOWN: return "solver breakdown";
+    case HISQ_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown error";
+}
+
+const char* hisq_last_error(void) { return g_last_error; }
+
+int hisq_create(hisq_ctx** out, const int dims[4], unsigned prec_mask, void* stream) {
+  if (!out || !dims) return set_error(HISQ_EINVAL, "null argument");
+  *out = nullptr;
+  long long V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 4 || (dims[m] & 1)) return set_error(HISQ_EINVAL, "extent %d of dimension %d must be even and >= 4", dims[m], m);
+    V *= dims[m];
+  }
+  if (V > (1LL << 30)) return set_error(HISQ_EINVAL, "volume %lld too large (max 2^30 sites)", V);
+  if (prec_mask & ~HISQ_PREC_ALL) return set_error(HISQ_EINVAL, "bad precision mask 0x%x", prec_mask);
+  hisq_ctx* c = new (std::nothrow) hisq_ctx();
+  if (!c) return set_error(HISQ_ENOMEM, "host allocation");
+  for (int m = 0; m < 4; ++m) c->g.L[m] = dims[m];
+  c->g.stride[0] = 1;
+  c->g.stride[1] = dims[0];
+  c->g.stride[2] = dims[0] * dims[1];
+  c->g.stride[3] = dims[0] * dims[1] * dims[2];
+  c->g.half_x = dims[0] / 2;
+  c->g.V = (int)V;
+  c->g.half = (int)(V / 2);
+  c->prec_mask = prec_mask | HISQ_PREC_BIT(HISQ_F64);
+  c->t_loaded.assign(dims[3], 0);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_error(e, "device query");
+  }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    // A blocking stream: ordered with the legacy default stream, and capturable.
+    e = cudaStreamCreate(&c->stream);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_error(e, "cudaStreamCreate");
+    }
+    c->own_stream = true;
+  }
+  int rc = HISQ_OK;
+  for (int p = 0; p < 4 && rc == HISQ_OK; ++p) {
+    if (!(c->prec_mask & HISQ_PREC_BIT(p))) continue;
+    size_t bytes = 16 * link_block_bytes(p, c->g.half);
+    e = cudaMalloc((void**)&c->links[p], bytes);
+    if (e != cudaSuccess) rc = cuda_error(e, "link storage");
+  }
+  if (rc == HISQ_OK) {
+    e = cudaMalloc((void**)&c->d_counters, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->pinned, 1 << 16);
+    if (e != cudaSuccess) rc = cuda_error(e, "context buffers");
+  }
+  if (rc != HISQ_OK) {
+    hisq_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return HISQ_OK;
+}
+
+int hisq_destroy(hisq_ctx* c) {
+  if (!c) return HISQ_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int p = 0; p < 4; ++p) cudaFree(c->links[p]);
+  for (auto& kv : c->ws) cudaFree(kv.second.ptr);
+  cudaFree(c->d_counters);
+  cudaFree(c->d_flag);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return HISQ_OK;
+}
+
+int hisq_load_links_slab(hisq_ctx* c, int t_begin, int t_count, const double* fat, const double* lng,
+                         unsigned flags) {
+  if (!c || !fat || !lng) return set_error(HISQ_EINVAL, "null argument");
+  if (t_begin < 0 || t_count < 1 || t_begin + t_count > c->g.L[3])
+    return set_error(HISQ_EINVAL, "t-slab [%d, %d) outside [0, %d)", t_begin, t_begin + t_count, c->g.L[3]);
+  if (flags & ~(HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T)) return set_error(HISQ_EINVAL, "bad flags 0x%x", flags);
+  bool any = false;
+  for (unsigned char v : c->t_loaded) any = any || v;
+  if (any && flags != c->load_flags) return set_error(HISQ_EINVAL, "flags differ from the slabs already loaded");
+  c->load_flags = flags;
+  const size_t slice = (size_t)c->g.L[0] * c->g.L[1] * c->g.L[2] * 4 * 9 * 2;  // doubles per t-slice
+  // chunks of t-slices bounded to ~512 MB of staging per kind
+  int chunk = (int)((512u << 20) / (slice * sizeof(double)));
+  if (chunk < 1) chunk = 1;
+  if (chunk > t_count) chunk = t_count;
+  double* d_fat = (double*)workspace(c, "stage_fat", chunk * slice * sizeof(double));
+  double* d_long = (double*)workspace(c, "stage_long", chunk * slice * sizeof(double));
+  if (!d_fat || !d_long) return set_error(HISQ_ENOMEM, "link staging buffers");
+  HISQ_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  c->links_ready = false;
+  for (int t = 0; t < t_count; t += chunk) {
+    int nt = t + chunk <= t_count ? chunk : t_count - t;
+    size_t off = (size_t)t * slice;
+    HISQ_CUDA(cudaMemcpyAsync(d_fat, fat + off, nt * slice * sizeof(double), cudaMemcpyDefault, c->stream));
+    HISQ_CUDA(cudaMemcpyAsync(d_long, lng + off, nt * slice * sizeof(double), cudaMemcpyDefault, c->stream));
+    int rc = pack_links_slab(c, d_fat, d_long, t_begin + t, nt, flags);
+    if (rc != HISQ_OK) return rc;
+  }
+  int bad = 0;
+  HISQ_CUDA(cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  HISQ_CUDA(cudaStreamSynchronize(c->stream));
+  if (bad) {
+    for (auto& v : c->t_loaded) v = 0;
+    return set_error(HISQ_ENONFINITE, "non-finite link entries in t-slab [%d, %d)", t_begin, t_begin + t_count);
+  }
+  for (int t = t_begin; t < t_begin + t_count; ++t) c->t_loaded[t] = 1;
+  bool all = true;
+  for (unsigned char v : c->t_loaded) all = all && v;
+  c->links_ready = all;
+  return HISQ_OK;
+}
+
+int hisq_load_links(hisq_ctx* c, const double* fat, const double* lng, unsigned flags) {
+  if (!c) return set_error(HISQ_EINVAL, "null context");
+  for (auto& v : c->t_loaded) v = 0;
+  return hisq_load_links_slab(c, 0, c->g.L[3], fat, lng, flags);
+}
+
+static int check_vec_args(hisq_ctx* c, int prec, int nrhs) {
+  if (!c) return set_error(HISQ_EINVAL, "null context");
+  if (prec < 0 || prec > 3) return set_error(HISQ_EINVAL, "bad precision %d", prec);
+  if (!c->links[prec]) return set_error(HISQ_EINVAL, "precision %d not resident", prec);
+  if (nrhs < 1 || nrhs > 64) return set_error(HISQ_EINVAL, "nrhs %d outside [1, 64]", nrhs);
+  if (!c->links_ready) return set_error(HISQ_ENOLINKS, "links not loaded");
+  return HISQ_OK;
+}
+
+static size_t vec_bytes(const hisq_ctx* c, int prec, int nrhs) {
+  return (size_t)nrhs * c->g.half * 6 * real_size(prec);
+}
+
+static bool aligned(const void* p, int prec) {
+  size_t a = prec == HISQ_F64 ? 16 : prec == HISQ_F32 ? 8 : 4;
+  return ((uintptr_t)p % a) == 0;
+}
+
+// Resolve a possibly-host vector to a device pointer (copying host input in).
+static int stage_in(hisq_ctx* c, const void* p, size_t bytes, const char* name, const void** dev) {
+  if (is_device_ptr(p)) {
+    *dev = p;
+    return HISQ_OK;
+  }
+  void* d = workspace(c, name, bytes);
+  if (!d) return set_error(HISQ_ENOMEM, "staging buffer %s", name);
+  HISQ_CUDA(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, c->stream));
+  *dev = d;
+  return HISQ_OK;
+}
+
+int hisq_dslash(hisq_ctx* c, int out_parity, void* out, const void* in, int prec, int nrhs) {
+  int rc = check_vec_args(c, prec, nrhs);
+  if (rc != HISQ_OK) return rc;
+  if (out_parity != 0 && out_parity != 1) return set_error(HISQ_EINVAL, "parity %d", out_parity);
+  if (!out || !in || out == in) return set_error(HISQ_EINVAL, "null or aliased vectors");
+  if (!aligned(out, prec) || !aligned(in, prec)) return set_error(HISQ_EINVAL, "misaligned vector");
+  const size_t bytes = vec_bytes(c, prec, nrhs);
+  const void* d_in;
+  if ((rc = stage_in(c, in, bytes, "stage_in", &d_in)) != HISQ_OK) return rc;
+  bool host_out = !is_device_ptr(out);
+  void* d_out = host_out ? workspace(c, "stage_out", bytes) : out;
+  if (!d_out) return set_error(HISQ_ENOMEM, "staging buffer");
+  DslashCall call;
+  call.out_parity = out_parity;
+  call.out = d_out;
+  call.in = d_in;
+  call.nrhs = nrhs;
+  call.rhs_stride = c->g.half;
+  rc = dslash_launch(c, prec, prec, call);
+  if (rc != HISQ_OK) return rc;
+  if (host_out) {
+    HISQ_CUDA(cudaMemcpyAsync(out, d_out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    HISQ_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return HISQ_OK;
+}
+
+int hisq_apply_A(hisq_ctx* c, void* out, const void* in, double mass, double sigma, int prec, int nrhs) {
+  int rc = check_vec_args(c, prec, nrhs);
+  if (rc != HISQ_OK) return rc;
+  if (!out || !in || out == in) return set_error(HISQ_EINVAL, "null or aliased vectors");
+  if (!aligned(out, prec) || !aligned(in, prec)) return set_error(HISQ_EINVAL, "misaligned vector");
+  if (!(mass >= 0) || !(sigma >= 0)) return set_error(HISQ_EINVAL, "mass and sigma must be >= 0");
+  const size_t bytes = vec_bytes(c, prec, nrhs);
+  const void* d_in;
+  if ((rc = stage_in(c, in, bytes, "stage_in", &d_in)) != HISQ_OK) return rc;
+  bool host_out = !is_device_ptr(out);
+  void* d_out = host_out ? workspace(c, "stage_out", bytes) : out;
+  void* tmp = workspace(c, "apply_tmp", bytes);
+  if (!d_out || !tmp) return set_error(HISQ_ENOMEM, "workspace");
+  DslashCall c1;
+  c1.out_parity = 1;
+  c1.out = tmp;
+  c1.in = d_in;
+  c1.nrhs = nrhs;
+  c1.rhs_stride = c->g.half;
+  if ((rc = dslash_launch(c, prec, prec, c1)) != HISQ_OK) return rc;
+  DslashCall c2 = c1;
+  c2.out_parity = 0;
+  c2.out = d_out;
+  c2.in = tmp;
+  c2.y = d_in;
+  c2.a = 4.0 * mass * mass + sigma;
+  c2.epi = EPI_AXPY;
+  if ((rc = dslash_launch(c, prec, prec, c2)) != HISQ_OK) return rc;
+  if (host_out) {
+    HISQ_CUDA(cudaMemcpyAsync(out, d_out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    HISQ_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return HISQ_OK;
+}
+
+long long hisq_launch_count(const hisq_ctx* c) { return c ? c->launches : 0; }
+
+double hisq_dslash_bytes(const hisq_ctx* c, int prec, int nrhs) {
+  if (!c || prec < 0 || prec > 3) return 0.0;
+  return dslash_bytes(c, prec, prec, nrhs);
+}
+
+int hisq_set_autotune(hisq_ctx* c, int enable) {
+  if (!c) return set_error(HISQ_EINVAL, "null context");
+  c->autotune = enable ? 1 : 0;
+  return HISQ_OK;
+}
+
+int hisq_tune_report(const hisq_ctx* c, char* buf, size_t len) {
+  if (!c || !buf || len == 0) return set_error(HISQ_EINVAL, "null argument");
+  size_t used = 0;
+  buf[0] = 0;
+  for (auto& kv : c->tune) {
+    int n = snprintf(buf + used, len - used, "%s %dx%dx%dx%d -> %d\n", kv.first.c_str(), c->g.L[0], c->g.L[1],
+                     c->g.L[2], c->g.L[3], kv.second);
+    if (n < 0 || (size_t)n >= len - used) break;
+    used += n;
+  }
+  return HISQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,874 @@
+// CG on A = 4 m^2 - D_eo D_oe (Sec. 2 module list: CG with multi-RHS and mixed-precision
+// variants; Sec. 3: the CG that takes about 60% of HISQ RHMC time).
+//
+// One iteration, for every rhs r at once:
+//   t     = D_oe p                                   (Dslash, odd output)
+//   Ap    = 4m^2 p - D_eo t,  pAp = Re<p, Ap>         (Dslash with fused axpy + FP64 dot)
+//   alpha = rr / pAp;  x += alpha*scale*p;  r -= alpha*Ap;  rr' = |r|^2     (k_update)
+//   beta  = rr' / rr;  p = r + beta*p;  rr = rr'; convergence flags        (k_pupdate)
+// Plain FP64 CG keeps r, p, Ap in FP64 with FP64 links. Mixed precision keeps r, p, Ap in
+// FP32 with links in the inner precision (FP32, FP16 or BF16 storage) and FP32 arithmetic;
+// x, the reductions and the reliable update r = b - A x (FP64 links) stay FP64. Reliable
+// update (a reading of the paper's "mixed precision" CG, which it names without detail):
+// every reliable_period inner iterations, or as soon as the inner residual says the
+// tolerance is met, recompute the true residual in FP64, rescale it to unit RMS entry,
+// and restart the search direction from it (p = r). Keeping the old direction would pair
+// alpha = |r_true|^2 / <p, A p> with a p built from the drifted iterated residual, which
+// overshoots whenever the low-precision operator has let the two residuals part.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "solver_common.cuh"
+#include "tune.h"
+
+namespace hisq {
+
+int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c);
+double dslash_bytes(const hisq_ctx* ctx, int lp, int sp, int nrhs);
+bool is_device_ptr(const void* p);
+
+// ------------------------------------------------------------------ kernels
+// r = b - Ax (all FP64); rr_true = |r|^2; with init, bb = |b|^2.
+__global__ void k_residual(const double2* __restrict__ b, size_t b_stride, const double2* __restrict__ Ax,
+                           double2* __restrict__ r, size_t n /* complex entries per rhs */, SolverState* st,
+                           double* partials, size_t pstride, unsigned* counter, int init) {
+  const int rh = blockIdx.y;
+  const size_t off = (size_t)rh * n;
+  const double2* bq = b + (size_t)rh * b_stride;
+  double v[2] = {0.0, 0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double2 bv = bq[i], av = Ax[off + i];
+    double2 rv = make_double2(bv.x - av.x, bv.y - av.y);
+    r[off + i] = rv;
+    v[0] += rv.x * rv.x + rv.y * rv.y;
+    v[1] += bv.x * bv.x + bv.y * bv.y;
+  }
+  double out[2][MAXR];
+  if (grid_reduce<2>(v, partials, pstride, counter, out, st->nrhs) && threadIdx.x == 0) {
+    for (int q = 0; q < st->nrhs; ++q) {
+      st->rr_true[q] = out[0][q];
+      if (init) st->bb[q] = out[1][q];
+      if (!isfinite(out[0][q])) st->nonfinite = 1;
+    }
+  }
+}
+
+// Reliable update: for each rhs not yet verified, r_lo = r_hi / s (s = RMS entry of r_hi),
+// p = r_lo (restart); rr = |r_hi|^2 / s^2. Verified rhs are frozen.
+template <typename S>
+__global__ void k_reliable(const double2* __restrict__ r_hi, S* __restrict__ r_lo, S* __restrict__ p, size_t n,
+                           SolverState* st, int first, unsigned* counter) {
+  const int rh = blockIdx.y;
+  const size_t off = (size_t)rh * n;
+  const bool conv = st->rr_true[rh] <= st->tol2[rh];
+  const double s_new = sqrt(st->rr_true[rh] / (double)n);
+  (void)first;
+  if (!conv && s_new > 0.0) {
+    const double inv = 1.0 / s_new;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      double2 rv = r_hi[off + i];
+      const S re = S(rv.x * inv), im = S(rv.y * inv);
+      r_lo[2 * (off + i)] = re;
+      r_lo[2 * (off + i) + 1] = im;
+      p[2 * (off + i)] = re;
+      p[2 * (off + i) + 1] = im;
+    }
+  }
+  if (last_block_done(counter) && threadIdx.x == 0) {
+    bool all = true;
+    for (int q = 0; q < st->nrhs; ++q) {
+      const bool c = st->rr_true[q] <= st->tol2[q];
+      st->rhs_conv[q] = c;
+      st->rhs_done[q] = c;
+      const double s = sqrt(st->rr_true[q] / (double)n);
+      if (!c && s > 0.0) {
+        st->scale[q] = s;
+        st->rr[q] = st->rr_true[q] / (s * s);
+      }
+      all = all && c;
+    }
+    st->done = all ? 1 : 0;
+    st->cycle_iter = 0;
+  }
+}
+
+// x += alpha*scale*p; r -= alpha*Ap; rr_new = |r|^2.
+template <typename S>
+__global__ void k_update(double2* __restrict__ x, S* __restrict__ r, const S* __restrict__ p,
+                         const S* __restrict__ Ap, size_t n, SolverState* st, double* partials, size_t pstride,
+                         unsigned* counter) {
+  if (st->done) return;
+  using T = typename Real<S>::acc;
+  const int rh = blockIdx.y;
+  const size_t off = (size_t)rh * n;
+  double v[1] = {0.0};
+  const double pap = st->pAp[rh];
+  const bool active = !st->rhs_done[rh] && pap > 0.0 && isfinite(pap);
+  const double alpha = active ? st->rr[rh] / pap : 0.0;
+  const double ax = alpha * st->scale[rh];
+  const T a = T(alpha);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = 2 * (off + i);
+    T pr = T(p[j]), pi = T(p[j + 1]);
+    T rr_ = T(r[j]), ri = T(r[j + 1]);
+    if (active) {
+      double2 xv = x[off + i];
+      xv.x += ax * (double)pr;
+      xv.y += ax * (double)pi;
+      x[off + i] = xv;
+      rr_ = fma(-a, T(Ap[j]), rr_);
+      ri = fma(-a, T(Ap[j + 1]), ri);
+      r[j] = S(rr_);
+      r[j + 1] = S(ri);
+    }
+    v[0] += (double)rr_ * (double)rr_ + (double)ri * (double)ri;
+  }
+  double out[1][MAXR];
+  if (grid_reduce<1>(v, partials, pstride, counter, out, st->nrhs) && threadIdx.x == 0) {
+    for (int q = 0; q < st->nrhs; ++q) {
+      st->rr_new[q] = out[0][q];
+      const double pq = st->pAp[q];
+      if (!st->rhs_done[q] && !(pq > 0.0)) st->breakdown = 1;
+      if (!isfinite(out[0][q])) st->nonfinite = 1;
+    }
+  }
+}
+
+// p = r + beta*p with beta = rr_new / rr; then (last block) commit rr, iteration counts,
+// per-rhs inner convergence and the end-of-cycle flag.
+template <typename S>
+__global__ void k_pupdate(const S* __restrict__ r, S* __restrict__ p, size_t n, SolverState* st, unsigned* counter) {
+  if (st->done) return;
+  using T = typename Real<S>::acc;
+  const int rh = blockIdx.y;
+  const size_t off = (size_t)rh * n;
+  if (!st->rhs_done[rh]) {
+    const T beta = T(st->rr_new[rh] / st->rr[rh]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      const size_t j = 2 * (off + i);
+      p[j] = S(fma(beta, T(p[j]), T(r[j])));
+      p[j + 1] = S(fma(beta, T(p[j + 1]), T(r[j + 1])));
+    }
+  }
+  if (last_block_done(counter) && threadIdx.x == 0) {
+    bool all = true;
+    for (int q = 0; q < st->nrhs; ++q) {
+      if (!st->rhs_done[q]) {
+        st->rr[q] = st->rr_new[q];
+        const double s = st->scale[q];
+        if (st->rr[q] * s * s <= st->tol2[q]) st->rhs_done[q] = 1;
+      }
+      all = all && st->rhs_done[q];
+    }
+    st->iter += 1;
+    st->cycle_iter += 1;
+    if (all || st->cycle_iter >= st->cycle_limit || st->breakdown || st->nonfinite) st->done = 1;
+  }
+}
+
+__global__ void k_new_cycle(SolverState* st) {
+  st->done = 0;
+  st->cycle_iter = 0;
+}
+
+// ------------------------------------------------------------------ host driver
+struct CgBuffers {
+  double2 *x, *b, *r_hi, *Ax, *t64;
+  size_t b_stride;          // complex entries between sources (0: one source for every rhs)
+  std::vector<double> a;    // per-rhs diagonal 4m^2 + sigma_r
+  void *r, *p, *Ap, *t;  // inner vectors (S = double or float)
+  SolverState* st;
+  double* partials;
+};
+
+static dim3 blas_grid(const hisq_ctx* ctx, int nrhs) {
+  int gx = (int)((ctx->g.half * 3 + 255) / 256);
+  int cap = ctx->num_sms * 8 / nrhs;
+  if (cap < 4) cap = 4;
+  if (gx > cap) gx = cap;
+  return dim3(gx, nrhs);
+}
+
+// r_hi = b - A_64 x; rr_true (and bb with init).
+static int true_residual(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int init) {
+  const size_t n = (size_t)ctx->g.half * 3;
+  DslashCall c1;
+  c1.out_parity = 1;
+  c1.out = B.t64;
+  c1.in = B.x;
+  c1.nrhs = nrhs;
+  c1.rhs_stride = ctx->g.half;
+  int rc = dslash_launch(ctx, HISQ_F64, HISQ_F64, c1);
+  if (rc != HISQ_OK) return rc;
+  DslashCall c2 = c1;
+  c2.out_parity = 0;
+  c2.out = B.Ax;
+  c2.in = B.t64;
+  c2.y = B.x;
+  c2.a_rhs = B.a.data();
+  c2.epi = EPI_AXPY;
+  if ((rc = dslash_launch(ctx, HISQ_F64, HISQ_F64, c2)) != HISQ_OK) return rc;
+  k_residual<<<blas_grid(ctx, nrhs), 256, 0, ctx->stream>>>(B.b, B.b_stride, B.Ax, B.r_hi, n, B.st, B.partials,
+                                                            partial_stride(ctx), ctx->d_counters + 1, init);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx);
+  return HISQ_OK;
+}
+
+template <typename S>
+static int reliable(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int first) {
+  const size_t n = (size_t)ctx->g.half * 3;
+  k_reliable<S><<<blas_grid(ctx, nrhs), 256, 0, ctx->stream>>>(B.r_hi, (S*)B.r, (S*)B.p, n, B.st, first,
+                                                               ctx->d_counters + 2);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx);
+  return HISQ_OK;
+}
+
+// One inner iteration (inner link precision lp, spinor type S).
+template <typename S>
+static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
+  const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
+  const size_t n = (size_t)ctx->g.half * 3;
+  DslashCall c1;
+  c1.out_parity = 1;
+  c1.out = B.t;
+  c1.in = B.p;
+  c1.nrhs = nrhs;
+  c1.rhs_stride = ctx->g.half;
+  int rc = dslash_launch(ctx, lp, sp, c1);
+  if (rc != HISQ_OK) return rc;
+  DslashCall c2 = c1;
+  c2.out_parity = 0;
+  c2.out = B.Ap;
+  c2.in = B.t;
+  c2.y = B.p;
+  c2.a_rhs = B.a.data();
+  c2.epi = EPI_AXPY;
+  c2.partials = B.partials + 2 * MAXR * partial_stride(ctx);
+  c2.dot_out = B.st->pAp;
+  c2.counter = ctx->d_counters + 3;
+  if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
+  dim3 grid = blas_grid(ctx, nrhs);
+  k_update<S><<<grid, 256, 0, ctx->stream>>>(B.x, (S*)B.r, (const S*)B.p, (const S*)B.Ap, n, B.st, B.partials,
+                                             partial_stride(ctx), ctx->d_counters + 4);
+  k_pupdate<S><<<grid, 256, 0, ctx->stream>>>((const S*)B.r, (S*)B.p, n, B.st, ctx->d_counters + 5);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx, 2);
+  return HISQ_OK;
+}
+
+// CG for nrhs systems (A + sigma_r) x_r = b_r at once. x: device FP64 [nrhs][half][3]
+// (initial guess in, solution out); b: device FP64 sources with b_stride complex entries
+// between consecutive sources (0: one source for all rhs). sigma, tol: host arrays [nrhs].
+template <typename S>
+static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, int nrhs, double mass,
+                  const double* sigma, const double* tol, int maxiter, const hisq_solver_opts& o,
+                  hisq_solver_stats* stats) {
+  auto t_start = std::chrono::steady_clock::now();
+  const int lp = o.inner_prec;
+  const bool mixed = lp != HISQ_F64;
+  const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
+  const size_t n = (size_t)ctx->g.half * 3;
+  const size_t vb64 = (size_t)nrhs * n * sizeof(double2);
+  const size_t vbS = (size_t)nrhs * n * 2 * sizeof(S);
+  CgBuffers B;
+  B.x = x;
+  B.b = const_cast<double2*>(b);
+  B.b_stride = b_stride;
+  B.r_hi = (double2*)workspace(ctx, "cg_rhi", vb64);
+  B.Ax = (double2*)workspace(ctx, "cg_Ax", vb64);
+  B.t64 = (double2*)workspace(ctx, "cg_t64", vb64);
+  B.r = workspace(ctx, "cg_r", vbS);
+  B.p = workspace(ctx, "cg_p", vbS);
+  B.Ap = workspace(ctx, "cg_Ap", vbS);
+  B.t = workspace(ctx, "cg_t", vbS);
+  B.st = (SolverState*)workspace(ctx, "cg_state", sizeof(SolverState));
+  B.partials = (double*)workspace(ctx, "cg_partials", 3 * MAXR * partial_stride(ctx) * sizeof(double));
+  SolverState* hst = (SolverState*)ctx->pinned;
+  if (!B.r_hi || !B.Ax || !B.t64 || !B.r || !B.p || !B.Ap || !B.t || !B.st || !B.partials)
+    return set_error(HISQ_ENOMEM, "solver workspace");
+  B.a.resize(nrhs);
+  for (int q = 0; q < nrhs; ++q) B.a[q] = 4.0 * mass * mass + (sigma ? sigma[q] : 0.0);
+  long long dcalls = 0;
+  double dbytes = 0.0;
+
+  memset(hst, 0, sizeof(SolverState));
+  hst->nrhs = nrhs;
+  hst->cycle_limit = mixed ? o.reliable_period : o.poll_every;
+  for (int q = 0; q < nrhs; ++q) hst->scale[q] = 1.0;
+  HISQ_CUDA(cudaMemcpyAsync(B.st, hst, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
+  int rc = true_residual(ctx, B, nrhs, 1);
+  if (rc != HISQ_OK) return rc;
+  dcalls += 2;
+  dbytes += 2 * dslash_bytes(ctx, HISQ_F64, HISQ_F64, nrhs);
+  HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
+  HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int q = 0; q < nrhs; ++q) {
+    if (!isfinite(hst->bb[q]) || !isfinite(hst->rr_true[q]))
+      return set_error(HISQ_ENONFINITE, "non-finite source or initial guess (rhs %d)", q);
+    hst->tol2[q] = tol[q] * tol[q] * hst->bb[q];
+  }
+  HISQ_CUDA(cudaMemcpyAsync(B.st, hst, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
+  if ((rc = reliable<S>(ctx, B, nrhs, 1)) != HISQ_OK) return rc;
+
+  // pre-tune the inner Dslash launches outside any capture (they are idempotent)
+  {
+    DslashCall c1;
+    c1.out_parity = 1;
+    c1.out = B.t;
+    c1.in = B.p;
+    c1.nrhs = nrhs;
+    c1.rhs_stride = ctx->g.half;
+    if ((rc = dslash_launch(ctx, lp, sp, c1)) != HISQ_OK) return rc;
+    DslashCall c2 = c1;
+    c2.out_parity = 0;
+    c2.out = B.Ap;
+    c2.in = B.t;
+    c2.y = B.p;
+    c2.a_rhs = B.a.data();
+    c2.epi = EPI_AXPY;
+    c2.partials = B.partials + 2 * MAXR * partial_stride(ctx);
+    c2.dot_out = B.st->pAp;
+    c2.counter = ctx->d_counters + 3;
+    if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
+  }
+
+  const int cycle = hst->cycle_limit;
+  cudaGraphExec_t exec = nullptr;
+  long long graph_nodes = 0;
+  if (o.use_graph) {
+    cudaGraph_t graph;
+    HISQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    int crc = HISQ_OK;
+    for (int i = 0; i < cycle && crc == HISQ_OK; ++i) crc = iteration<S>(ctx, B, lp, nrhs);
+    ctx->capturing = false;
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (crc != HISQ_OK) return crc;
+    HISQ_CUDA(ce);
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    graph_nodes = (long long)nodes;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HISQ_CUDA(ce);
+  }
+  auto run_cycle = [&]() -> int {
+    if (exec) {
+      HISQ_CUDA(cudaGraphLaunch(exec, ctx->stream));
+      ctx->launches += graph_nodes;
+      return HISQ_OK;
+    }
+    for (int i = 0; i < cycle; ++i) {
+      int r2 = iteration<S>(ctx, B, lp, nrhs);
+      if (r2 != HISQ_OK) return r2;
+    }
+    return HISQ_OK;
+  };
+
+  int status = HISQ_OK;
+  int reliable_updates = 0;
+  HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
+  HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  bool converged = hst->done != 0;
+  bool verified = true;  // rr_true reflects the current x
+  int last_iter = 0;
+  while (!converged) {
+    if (hst->iter >= maxiter) {
+      status = HISQ_ENOCONV;
+      break;
+    }
+    if ((rc = run_cycle()) != HISQ_OK) {
+      status = rc;
+      break;
+    }
+    verified = false;
+    HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int done_iters = hst->iter - last_iter;
+    last_iter = hst->iter;
+    dcalls += 2LL * done_iters;
+    dbytes += 2.0 * done_iters * dslash_bytes(ctx, lp, sp, nrhs);
+    if (hst->nonfinite) {
+      status = set_error(HISQ_ENONFINITE, "non-finite residual at iteration %d", hst->iter);
+      break;
+    }
+    if (hst->breakdown) {
+      status = set_error(HISQ_EBREAKDOWN, "<p, A p> <= 0 at iteration %d", hst->iter);
+      break;
+    }
+    bool all_inner = true;
+    for (int q = 0; q < nrhs; ++q) all_inner = all_inner && hst->rhs_done[q];
+    if (mixed || all_inner) {
+      if ((rc = true_residual(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
+      if ((rc = reliable<S>(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
+      dcalls += 2;
+      dbytes += 2 * dslash_bytes(ctx, HISQ_F64, HISQ_F64, nrhs);
+      ++reliable_updates;
+      verified = true;
+      HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
+      HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+      converged = true;
+      for (int q = 0; q < nrhs; ++q) converged = converged && hst->rhs_conv[q];
+    } else {
+      k_new_cycle<<<1, 1, 0, ctx->stream>>>(B.st);
+      HISQ_CUDA(cudaGetLastError());
+      note_launch(ctx);
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (!verified) {
+    // the iterate changed since the last true residual: recompute it for the report
+    if ((rc = true_residual(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
+    HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  double worst = 0.0;
+  for (int q = 0; q < nrhs; ++q) {
+    double rel = hst->bb[q] > 0 ? sqrt(hst->rr_true[q] / hst->bb[q]) : sqrt(hst->rr_true[q]);
+    if (rel > worst) worst = rel;
+    if (stats && q < 64) stats->shift_residual[q] = rel;
+  }
+  if (stats) {
+    stats->iters += hst->iter;
+    stats->reliable_updates += reliable_updates;
+    stats->converged = converged && status == HISQ_OK;
+    stats->true_rel_residual = worst;
+    stats->seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    stats->dslash_bytes += dbytes;
+    stats->dslash_calls += dcalls;
+  }
+  if (status == HISQ_ENOCONV)
+    return set_error(HISQ_ENOCONV, "no convergence in %d iterations (true residual %.3e)", hst->iter, worst);
+  return status;
+}
+
+// ------------------------------------------------------------------ multi-shift CG
+// Shifted systems (A + sigma_k) x_k = b share the Krylov space of the base system (smallest
+// shift): r_k = zeta_k r. Per base iteration j (Jegerlehner's recurrences, hep-lat/9612014):
+//   zeta_k' = zeta_k zeta_k^old alpha_old / (alpha beta_old (zeta_k^old - zeta_k)
+//                                            + zeta_k^old alpha_old (1 + (sigma_k - sigma_0) alpha))
+//   alpha_k = alpha zeta_k'/zeta_k,  x_k += alpha_k p_k,
+//   beta_k  = beta (zeta_k'/zeta_k)^2,  p_k = zeta_k' r + beta_k p_k.
+struct MsState {
+  double sigma[MAXR], zeta[MAXR], zeta_old[MAXR], zeta_new[MAXR], alpha_k[MAXR], beta_k[MAXR], tol2[MAXR];
+  int active[MAXR], conv_iter[MAXR];
+  double rr, rr_new, pAp, bb, alpha, alpha_old, beta_old, scale;
+  int base, nshift, iter, done, cycle_iter, cycle_limit, breakdown, nonfinite;
+};
+
+// r -= alpha Ap (alpha = rr / pAp), rr_new = |r|^2; last block: every shift's recurrence scalars.
+template <typename S>
+__global__ void k_ms_rupdate(S* __restrict__ r, const S* __restrict__ Ap, size_t n, MsState* st, double* partials,
+                             size_t pstride, unsigned* counter) {
+  if (st->done) return;
+  using T = typename Real<S>::acc;
+  const double pap = st->pAp;
+  const double alpha = (pap > 0.0 && isfinite(pap)) ? st->rr / pap : 0.0;
+  const T a = T(alpha);
+  double v = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    T re = fma(-a, T(Ap[2 * i]), T(r[2 * i]));
+    T im = fma(-a, T(Ap[2 * i + 1]), T(r[2 * i + 1]));
+    r[2 * i] = S(re);
+    r[2 * i + 1] = S(im);
+    v += (double)re * (double)re + (double)im * (double)im;
+  }
+  __shared__ double red[32];
+  double s = block_sum_dyn(v, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (!last_block_done(counter)) return;
+  double tot = sum_partials_dyn(partials, gridDim.x, red);
+  if (threadIdx.x != 0) return;
+  if (!(pap > 0.0)) st->breakdown = 1;
+  if (!isfinite(tot)) st->nonfinite = 1;
+  st->rr_new = tot;
+  st->alpha = alpha;
+  const double beta = tot / st->rr;
+  const double s0 = st->sigma[st->base];
+  for (int k = 0; k < st->nshift; ++k) {
+    if (!st->active[k]) continue;
+    double zn;
+    if (k == st->base) {
+      zn = 1.0;
+    } else {
+      const double z = st->zeta[k], zo = st->zeta_old[k];
+      const double den = alpha * st->beta_old * (zo - z) + zo * st->alpha_old * (1.0 + (st->sigma[k] - s0) * alpha);
+      zn = z * zo * st->alpha_old / den;
+    }
+    const double ratio = zn / st->zeta[k];
+    st->zeta_new[k] = zn;
+    st->alpha_k[k] = alpha * ratio;
+    st->beta_k[k] = beta * ratio * ratio;
+  }
+}
+
+// For every active shift: x_k += alpha_k*scale*p_k; p_k = zeta_k' r + beta_k p_k (r read once).
+// Last block: commit the recurrences, freeze converged shifts, count the iteration.
+template <typename S>
+__global__ void k_ms_update(double2* __restrict__ x, S* __restrict__ p, const S* __restrict__ r, size_t n,
+                            MsState* st, unsigned* counter) {
+  if (st->done) return;
+  using T = typename Real<S>::acc;
+  __shared__ double s_ax[MAXR];
+  __shared__ T s_z[MAXR], s_b[MAXR];
+  __shared__ int s_act[MAXR];
+  const int ns = st->nshift;
+  for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+    s_act[k] = st->active[k];
+    s_ax[k] = st->alpha_k[k] * st->scale;
+    s_z[k] = T(st->zeta_new[k]);
+    s_b[k] = T(st->beta_k[k]);
+  }
+  __syncthreads();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T rre = T(r[2 * i]), rim = T(r[2 * i + 1]);
+    for (int k = 0; k < ns; ++k) {
+      if (!s_act[k]) continue;
+      const size_t j = (size_t)k * n + i;
+      const T pre = T(p[2 * j]), pim = T(p[2 * j + 1]);
+      double2 xv = x[j];
+      xv.x += s_ax[k] * (double)pre;
+      xv.y += s_ax[k] * (double)pim;
+      x[j] = xv;
+      p[2 * j] = S(fma(s_b[k], pre, s_z[k] * rre));
+      p[2 * j + 1] = S(fma(s_b[k], pim, s_z[k] * rim));
+    }
+  }
+  if (!last_block_done(counter) || threadIdx.x != 0) return;
+  st->iter += 1;
+  st->cycle_iter += 1;
+  st->alpha_old = st->alpha;
+  st->beta_old = st->rr_new / st->rr;
+  st->rr = st->rr_new;
+  const double res2 = st->rr * st->scale * st->scale;
+  bool any_other = false;
+  for (int k = 0; k < ns; ++k) {
+    if (!st->active[k]) continue;
+    st->zeta_old[k] = st->zeta[k];
+    st->zeta[k] = st->zeta_new[k];
+    if (k != st->base && st->zeta[k] * st->zeta[k] * res2 <= st->tol2[k]) {
+      st->active[k] = 0;
+      st->conv_iter[k] = st->iter;
+    }
+    if (k != st->base && st->active[k]) any_other = true;
+  }
+  const int b0 = st->base;
+  if (st->active[b0] && !any_other && res2 <= st->tol2[b0]) {
+    st->active[b0] = 0;
+    st->conv_iter[b0] = st->iter;
+  }
+  const bool finished = !st->active[b0];
+  if (finished || st->cycle_iter >= st->cycle_limit || st->breakdown || st->nonfinite) st->done = 1;
+}
+
+// r = b / scale; p_k = r; x_k = 0.
+template <typename S>
+__global__ void k_ms_init(const double2* __restrict__ b, S* __restrict__ r, S* __restrict__ p,
+                          double2* __restrict__ x, size_t n, int ns, double inv_scale) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 bv = b[i];
+    const S re = S(bv.x * inv_scale), im = S(bv.y * inv_scale);
+    r[2 * i] = re;
+    r[2 * i + 1] = im;
+    for (int k = 0; k < ns; ++k) {
+      const size_t j = (size_t)k * n + i;
+      p[2 * j] = re;
+      p[2 * j + 1] = im;
+      x[j] = make_double2(0.0, 0.0);
+    }
+  }
+}
+
+// |b|^2 into out[0] (single rhs).
+__global__ void k_norm2(const double2* __restrict__ b, size_t n, double* partials, double* out, unsigned* counter) {
+  double v = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 bv = b[i];
+    v += bv.x * bv.x + bv.y * bv.y;
+  }
+  __shared__ double red[32];
+  double s = block_sum_dyn(v, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (last_block_done(counter)) {
+    double t = sum_partials_dyn(partials, gridDim.x, red);
+    if (threadIdx.x == 0) out[0] = t;
+  }
+}
+
+template <typename S>
+static int ms_iteration(hisq_ctx* ctx, int lp, double2* x, S* r, S* p, S* Ap, S* t, MsState* st, double* partials,
+                        double a_base, int base, int ns) {
+  const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
+  const size_t n = (size_t)ctx->g.half * 3;
+  S* pb = p + (size_t)base * n * 2;
+  DslashCall c1;
+  c1.out_parity = 1;
+  c1.out = t;
+  c1.in = pb;
+  c1.nrhs = 1;
+  c1.rhs_stride = ctx->g.half;
+  int rc = dslash_launch(ctx, lp, sp, c1);
+  if (rc != HISQ_OK) return rc;
+  DslashCall c2 = c1;
+  c2.out_parity = 0;
+  c2.out = Ap;
+  c2.in = t;
+  c2.y = pb;
+  c2.a = a_base;
+  c2.epi = EPI_AXPY;
+  c2.partials = partials + MAXR * partial_stride(ctx);
+  c2.dot_out = &st->pAp;
+  c2.counter = ctx->d_counters + 6;
+  if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
+  const int grid = blas_grid(ctx, 1).x;
+  k_ms_rupdate<S><<<grid, 256, 0, ctx->stream>>>(r, Ap, n, st, partials, partial_stride(ctx), ctx->d_counters + 7);
+  k_ms_update<S><<<grid, 256, 0, ctx->stream>>>(x, p, r, n, st, ctx->d_counters + 8);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx, 2);
+  (void)ns;
+  return HISQ_OK;
+}
+
+template <typename S>
+static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, const double* shifts, double mass,
+                          const double* tol, int maxiter, const hisq_solver_opts& o, hisq_solver_stats* stats) {
+  auto t_start = std::chrono::steady_clock::now();
+  const int lp = o.inner_prec;
+  const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
+  const size_t n = (size_t)ctx->g.half * 3;
+  S* r = (S*)workspace(ctx, "ms_r", n * 2 * sizeof(S));
+  S* Ap = (S*)workspace(ctx, "ms_Ap", n * 2 * sizeof(S));
+  S* t = (S*)workspace(ctx, "ms_t", n * 2 * sizeof(S));
+  S* p = (S*)workspace(ctx, "ms_p", (size_t)ns * n * 2 * sizeof(S));
+  MsState* st = (MsState*)workspace(ctx, "ms_state", sizeof(MsState));
+  double* partials = (double*)workspace(ctx, "ms_partials", 2 * MAXR * partial_stride(ctx) * sizeof(double));
+  if (!r || !Ap || !t || !p || !st || !partials) return set_error(HISQ_ENOMEM, "multi-shift workspace");
+  MsState* h = (MsState*)ctx->pinned;
+  int base = 0;
+  for (int k = 1; k < ns; ++k)
+    if (shifts[k] < shifts[base]) base = k;
+
+  // |b|^2 and the scale of the low-precision Krylov vectors (RMS entry of b -> 1)
+  const int grid1 = blas_grid(ctx, 1).x;
+  k_norm2<<<grid1, 256, 0, ctx->stream>>>(b, n, partials, (double*)ctx->pinned + 4096, ctx->d_counters + 9);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx);
+  HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  const double bb = ((double*)ctx->pinned)[4096];
+  if (!isfinite(bb)) return set_error(HISQ_ENONFINITE, "non-finite source");
+  if (bb == 0.0) {
+    HISQ_CUDA(cudaMemsetAsync(x, 0, (size_t)ns * n * sizeof(double2), ctx->stream));
+    return HISQ_OK;
+  }
+  const double scale = sqrt(bb / (double)n);
+  memset(h, 0, sizeof(MsState));
+  h->nshift = ns;
+  h->base = base;
+  h->bb = bb;
+  h->rr = bb / (scale * scale);
+  h->scale = scale;
+  h->alpha_old = 1.0;
+  h->beta_old = 0.0;
+  h->cycle_limit = o.poll_every;
+  for (int k = 0; k < ns; ++k) {
+    h->sigma[k] = shifts[k];
+    h->zeta[k] = h->zeta_old[k] = 1.0;
+    h->active[k] = 1;
+    h->conv_iter[k] = -1;
+    h->tol2[k] = tol[k] * tol[k] * bb;
+  }
+  HISQ_CUDA(cudaMemcpyAsync(st, h, sizeof(MsState), cudaMemcpyHostToDevice, ctx->stream));
+  k_ms_init<S><<<grid1, 256, 0, ctx->stream>>>(b, r, p, x, n, ns, 1.0 / scale);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx);
+  const double a_base = 4.0 * mass * mass + shifts[base];
+  // pre-tune outside capture
+  {
+    DslashCall c1;
+    c1.out_parity = 1;
+    c1.out = t;
+    c1.in = p + (size_t)base * n * 2;
+    c1.nrhs = 1;
+    c1.rhs_stride = ctx->g.half;
+    int rc = dslash_launch(ctx, lp, sp, c1);
+    if (rc != HISQ_OK) return rc;
+  }
+  const int cycle = o.poll_every;
+  cudaGraphExec_t exec = nullptr;
+  long long graph_nodes = 0;
+  if (o.use_graph) {
+    cudaGraph_t graph;
+    HISQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    int crc = HISQ_OK;
+    for (int i = 0; i < cycle && crc == HISQ_OK; ++i)
+      crc = ms_iteration<S>(ctx, lp, x, r, p, Ap, t, st, partials, a_base, base, ns);
+    ctx->capturing = false;
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (crc != HISQ_OK) return crc;
+    HISQ_CUDA(ce);
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    graph_nodes = (long long)nodes;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HISQ_CUDA(ce);
+  }
+  int status = HISQ_OK;
+  int last_iter = 0;
+  long long dcalls = 0;
+  double dbytes = 0.0;
+  for (;;) {
+    if (exec) {
+      HISQ_CUDA(cudaGraphLaunch(exec, ctx->stream));
+      ctx->launches += graph_nodes;
+    } else {
+      for (int i = 0; i < cycle; ++i) {
+        int rc = ms_iteration<S>(ctx, lp, x, r, p, Ap, t, st, partials, a_base, base, ns);
+        if (rc != HISQ_OK) return rc;
+      }
+    }
+    HISQ_CUDA(cudaMemcpyAsync(h, st, sizeof(MsState), cudaMemcpyDeviceToHost, ctx->stream));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    dcalls += 2LL * (h->iter - last_iter);
+    dbytes += 2.0 * (h->iter - last_iter) * dslash_bytes(ctx, lp, sp, 1);
+    last_iter = h->iter;
+    if (h->nonfinite) {
+      status = set_error(HISQ_ENONFINITE, "non-finite residual at iteration %d", h->iter);
+      break;
+    }
+    if (h->breakdown) {
+      status = set_error(HISQ_EBREAKDOWN, "<p, A p> <= 0 at iteration %d", h->iter);
+      break;
+    }
+    if (!h->active[base]) break;
+    if (h->iter >= maxiter) break;  // the verification below reports non-convergence
+    h->done = 0;
+    h->cycle_iter = 0;
+    HISQ_CUDA(cudaMemcpyAsync(&st->done, &h->done, 2 * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (stats) {
+    for (int k = 0; k < ns; ++k) stats->shift_iters[k] = h->conv_iter[k];
+    stats->iters = h->iter;
+    stats->dslash_calls = dcalls;
+    stats->dslash_bytes = dbytes;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  if (status != HISQ_OK) return status;
+  const int remaining = maxiter > h->iter ? maxiter - h->iter : 0;
+  // Verification in FP64 and, where a shift's true residual misses its tolerance, refinement:
+  // one multi-rhs CG over all shifts (per-rhs shift sigma_k, same source), so every link read
+  // serves all shifts. Inner precision as requested.
+  if (lp == HISQ_F64) return run_cg<double>(ctx, x, b, 0, ns, mass, shifts, tol, remaining, o, stats);
+  return run_cg<float>(ctx, x, b, 0, ns, mass, shifts, tol, remaining, o, stats);
+}
+
+}  // namespace hisq
+
+using namespace hisq;
+
+extern "C" {
+
+void hisq_solver_opts_default(hisq_solver_opts* o) {
+  if (!o) return;
+  o->inner_prec = HISQ_F64;
+  o->reliable_period = 50;
+  o->use_graph = 1;
+  o->poll_every = 25;
+}
+
+static int check_solver(hisq_ctx* ctx, const void* x, const void* b, double mass, int maxiter,
+                        const hisq_solver_opts* opts, hisq_solver_opts* o) {
+  if (!ctx || !x || !b) return set_error(HISQ_EINVAL, "null argument");
+  if (!ctx->links_ready) return set_error(HISQ_ENOLINKS, "links not loaded");
+  if (!(mass > 0) || maxiter < 0) return set_error(HISQ_EINVAL, "need mass > 0 and maxiter >= 0");
+  if ((uintptr_t)x % 16 || (uintptr_t)b % 16) return set_error(HISQ_EINVAL, "vectors must be 16-byte aligned");
+  hisq_solver_opts_default(o);
+  if (opts) *o = *opts;
+  if (o->inner_prec < 0 || o->inner_prec > 3 || !ctx->links[o->inner_prec])
+    return set_error(HISQ_EINVAL, "inner precision %d not resident", o->inner_prec);
+  if (o->reliable_period < 1 || o->poll_every < 1) return set_error(HISQ_EINVAL, "periods must be >= 1");
+  return HISQ_OK;
+}
+
+// Device views of caller vectors: device pointers are used in place; host vectors are
+// staged through workspaces and copied back (x only) on exit.
+struct Staged {
+  double2* x;
+  const double2* b;
+  bool x_host, b_host;
+};
+
+static int stage_solver(hisq_ctx* ctx, double* x, const double* b, size_t xb, size_t bbytes, bool copy_x, Staged* s) {
+  s->x_host = !is_device_ptr(x);
+  s->b_host = !is_device_ptr(b);
+  s->x = s->x_host ? (double2*)workspace(ctx, "user_x", xb) : (double2*)x;
+  s->b = s->b_host ? (const double2*)workspace(ctx, "user_b", bbytes) : (const double2*)b;
+  if (!s->x || !s->b) return set_error(HISQ_ENOMEM, "staging buffers");
+  if (s->x_host && copy_x) HISQ_CUDA(cudaMemcpyAsync(s->x, x, xb, cudaMemcpyHostToDevice, ctx->stream));
+  if (s->b_host) HISQ_CUDA(cudaMemcpyAsync((void*)s->b, b, bbytes, cudaMemcpyHostToDevice, ctx->stream));
+  return HISQ_OK;
+}
+
+static int unstage(hisq_ctx* ctx, double* x, size_t xb, const Staged& s, int rc) {
+  if (s.x_host) {
+    cudaError_t e = cudaMemcpyAsync(x, s.x, xb, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess && rc == HISQ_OK) return cuda_error(e, "copy-out of x");
+  }
+  return rc;
+}
+
+int hisq_cg(hisq_ctx* ctx, double* x, const double* b, int nrhs, double mass, double rel_tol, int maxiter,
+            const hisq_solver_opts* opts, hisq_solver_stats* stats) {
+  hisq_solver_opts o;
+  int rc = check_solver(ctx, x, b, mass, maxiter, opts, &o);
+  if (rc != HISQ_OK) return rc;
+  if (nrhs < 1 || nrhs > MAXR) return set_error(HISQ_EINVAL, "nrhs %d outside [1, %d]", nrhs, MAXR);
+  if (!(rel_tol > 0)) return set_error(HISQ_EINVAL, "rel_tol must be > 0");
+  if (stats) memset(stats, 0, sizeof *stats);
+  const size_t n = (size_t)ctx->g.half * 3, vb = (size_t)nrhs * n * sizeof(double2);
+  Staged s;
+  if ((rc = stage_solver(ctx, x, b, vb, vb, true, &s)) != HISQ_OK) return rc;
+  std::vector<double> tol(nrhs, rel_tol);
+  const long long l0 = ctx->launches;
+  if (o.inner_prec == HISQ_F64)
+    rc = run_cg<double>(ctx, s.x, s.b, n, nrhs, mass, nullptr, tol.data(), maxiter, o, stats);
+  else
+    rc = run_cg<float>(ctx, s.x, s.b, n, nrhs, mass, nullptr, tol.data(), maxiter, o, stats);
+  if (stats) stats->kernel_launches = ctx->launches - l0;
+  return unstage(ctx, x, vb, s, rc);
+}
+
+int hisq_multishift_cg(hisq_ctx* ctx, double* x, const double* b, int nshift, const double* shifts, double mass,
+                       const double* rel_tol, int maxiter, const hisq_solver_opts* opts, hisq_solver_stats* stats) {
+  hisq_solver_opts o;
+  int rc = check_solver(ctx, x, b, mass, maxiter, opts, &o);
+  if (rc != HISQ_OK) return rc;
+  if (nshift < 1 || nshift > MAXR || !shifts || !rel_tol)
+    return set_error(HISQ_EINVAL, "nshift %d outside [1, %d] or null shifts/tolerances", nshift, MAXR);
+  for (int k = 0; k < nshift; ++k)
+    if (!(shifts[k] >= 0) || !(rel_tol[k] > 0)) return set_error(HISQ_EINVAL, "shift %d: need sigma >= 0, tol > 0", k);
+  if (stats) memset(stats, 0, sizeof *stats);
+  const size_t n = (size_t)ctx->g.half * 3;
+  Staged s;
+  if ((rc = stage_solver(ctx, x, b, (size_t)nshift * n * sizeof(double2), n * sizeof(double2), false, &s)) != HISQ_OK)
+    return rc;
+  const long long l0 = ctx->launches;
+  if (o.inner_prec == HISQ_F64)
+    rc = run_multishift<double>(ctx, s.x, s.b, nshift, shifts, mass, rel_tol, maxiter, o, stats);
+  else
+    rc = run_multishift<float>(ctx, s.x, s.b, nshift, shifts, mass, rel_tol, maxiter, o, stats);
+  if (stats) stats->kernel_launches = ctx->launches - l0;
+  return unstage(ctx, x, (size_t)nshift * n * sizeof(double2), s, rc);
+}
+
+}  // extern "C"

@@ -1,0 +1,10 @@
+// Dslash instantiations with BF16 links: BF16 spinors or FP32 spinors. FP32 arithmetic.
+#include "dslash_launch.cuh"
+
+namespace hisq {
+int dslash_launch_bf16(hisq_ctx* ctx, int sp, const DslashCall& c) {
+  if (sp == HISQ_BF16) return dslash_launch_t<__nv_bfloat16, __nv_bfloat16>(ctx, c);
+  if (sp == HISQ_F32) return dslash_launch_t<__nv_bfloat16, float>(ctx, c);
+  return set_error(HISQ_EINVAL, "BF16 links pair with BF16 or FP32 spinors");
+}
+}  // namespace hisq

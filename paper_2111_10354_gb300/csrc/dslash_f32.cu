@@ -1,0 +1,9 @@
+// Dslash instantiations with FP32 links (FP32 spinors, FP32 arithmetic).
+#include "dslash_launch.cuh"
+
+namespace hisq {
+int dslash_launch_f32(hisq_ctx* ctx, int sp, const DslashCall& c) {
+  if (sp == HISQ_F32) return dslash_launch_t<float, float>(ctx, c);
+  return set_error(HISQ_EINVAL, "FP32 links pair with FP32 spinors only");
+}
+}  // namespace hisq

@@ -1,0 +1,148 @@
+// HISQ even/odd Dslash kernel (the stencil the paper calls "the most performance-critical
+// kernel" of its CG, Sec. 3): for each output site x of one parity,
+//   out(x) = sum_mu [ F_mu(x) in(x+mu) - F_mu(x-mu)^dag in(x-mu)
+//                   + L_mu(x) in(x+3mu) - L_mu(x-3mu)^dag in(x-3mu) ]
+// with staggered phases and the antiperiodic-t sign already folded into F and L.
+//
+// Design: one thread per output site (grid-stride), NR right-hand sides per thread so
+// every link is read from HBM once per launch however many vectors it is applied to
+// (the multi-RHS form, Sec. 3). Links stream through 16-byte no-L1-allocate loads from
+// their chunk planes; neighbour vectors go through L1/L2, where the 16-fold reuse of
+// each input site is served. Accumulation is FP64 for FP64 storage and FP32 otherwise.
+#pragma once
+#include "internal.cuh"
+
+namespace hisq {
+
+template <typename T>
+__device__ __forceinline__ void cmac_conj_sub(cplx<T>& acc, const cplx<T>& a, const cplx<T>& b) {
+  // acc -= conj(a) * b
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+
+struct DslashKArgs {
+  Geom g;
+  const char* links;  // resident link storage of the link precision (16 blocks)
+  size_t blk_bytes;   // bytes of one link block
+  int out_parity;
+  void* out;
+  const void* in;
+  size_t rhs_stride;  // sites between consecutive rhs vectors
+  const void* y;      // EPI_AXPY
+  double a[16];       // per-rhs diagonal coefficient 4m^2 + sigma_r
+  double* partials;   // [NR][gridDim.x]
+  double* dot_out;    // [NR]
+  unsigned* counter;
+};
+
+template <typename LR, typename SR, int NR, int EPI>
+__global__ void __launch_bounds__(NR <= 2 ? 512 : (NR <= 4 ? 256 : 128)) dslash_kernel(const DslashKArgs k) {
+  using A = typename Real<LR>::acc;  // accumulation type follows the link precision
+  using SA = typename Real<SR>::acc;
+  const Geom& g = k.g;
+  const int p = k.out_parity;
+  const char* fwd = k.links + (size_t)(p * 8) * k.blk_bytes;        // blocks of parity p
+  const char* bwd = k.links + (size_t)((1 - p) * 8) * k.blk_bytes;  // blocks of parity 1-p
+  double dot[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) dot[r] = 0.0;
+
+  for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.half; cb += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, p, cb, c);
+    const int idx = lex_index(g, c);
+    cplx<A> acc[NR][3];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc[r][i] = {A(0), A(0)};
+
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+      for (int kind = 0; kind < 2; ++kind) {
+        const int hop = kind == 0 ? 1 : 3;
+        const char* blk_f = fwd + (size_t)(kind * 4 + mu) * k.blk_bytes;
+        const char* blk_b = bwd + (size_t)(kind * 4 + mu) * k.blk_bytes;
+        // forward hop: + W_mu(x) in(x + hop mu)
+        {
+          const int nb = neighbour_cb(g, c, idx, mu, +hop);
+          cplx<A> U[9];
+          LinkIO<LR>::load(blk_f, g.half, cb, U);
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            cplx<SA> vs[3];
+            VecIO<SR>::load(k.in, (size_t)r * k.rhs_stride + nb, vs);
+            cplx<A> v[3] = {{A(vs[0].re), A(vs[0].im)}, {A(vs[1].re), A(vs[1].im)}, {A(vs[2].re), A(vs[2].im)}};
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int j = 0; j < 3; ++j) cmac(acc[r][i], U[3 * i + j], v[j]);
+          }
+        }
+        // backward hop: - W_mu(x - hop mu)^dag in(x - hop mu)
+        {
+          const int nb = neighbour_cb(g, c, idx, mu, -hop);
+          cplx<A> U[9];
+          LinkIO<LR>::load(blk_b, g.half, nb, U);
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            cplx<SA> vs[3];
+            VecIO<SR>::load(k.in, (size_t)r * k.rhs_stride + nb, vs);
+            cplx<A> v[3] = {{A(vs[0].re), A(vs[0].im)}, {A(vs[1].re), A(vs[1].im)}, {A(vs[2].re), A(vs[2].im)}};
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int j = 0; j < 3; ++j) cmac_conj_sub(acc[r][i], U[3 * j + i], v[j]);
+          }
+        }
+      }
+    }
+
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const size_t site = (size_t)r * k.rhs_stride + cb;
+      cplx<SA> o[3];
+      if (EPI == EPI_PLAIN) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) o[i] = {SA(acc[r][i].re), SA(acc[r][i].im)};
+      } else {
+        cplx<SA> yv[3];
+        VecIO<SR>::load(k.y, site, yv);
+        const A a = A(k.a[r]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          o[i].re = SA(fma(a, A(yv[i].re), -acc[r][i].re));
+          o[i].im = SA(fma(a, A(yv[i].im), -acc[r][i].im));
+        }
+        if (k.partials) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            dot[r] += (double)yv[i].re * (double)o[i].re + (double)yv[i].im * (double)o[i].im;
+        }
+      }
+      VecIO<SR>::store(k.out, site, o);
+    }
+  }
+
+  if (EPI == EPI_AXPY) {
+    if (k.partials == nullptr) return;  // uniform over the grid
+    __shared__ double red[32];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      double s = block_sum_dyn(dot[r], red);
+      if (threadIdx.x == 0) k.partials[(size_t)r * gridDim.x + blockIdx.x] = s;
+    }
+    if (last_block_done(k.counter)) {
+      for (int r = 0; r < NR; ++r) {
+        double s = sum_partials_dyn(k.partials + (size_t)r * gridDim.x, gridDim.x, red);
+        if (threadIdx.x == 0) k.dot_out[r] = s;
+      }
+    }
+  }
+}
+
+}  // namespace hisq

@@ -1,0 +1,79 @@
+// Host-side launcher of the Dslash kernel for one (link, spinor) precision pair: splits
+// nrhs into register-resident groups of NR right-hand sides and picks the block size
+// with the autotuner.
+#pragma once
+#include <string>
+
+#include "dslash_impl.cuh"
+#include "tune.h"
+
+namespace hisq {
+
+template <typename LR, typename SR, int NR, int EPI>
+static int launch_group(hisq_ctx* ctx, DslashKArgs a, const char* key) {
+  auto kern = dslash_kernel<LR, SR, NR, EPI>;
+  auto run = [&](int block) -> cudaError_t {
+    int grid = (ctx->g.half + block - 1) / block;
+    int cap = max_grid_blocks(ctx, block);
+    if (grid > cap) grid = cap;
+    kern<<<grid, block, 0, ctx->stream>>>(a);
+    return cudaGetLastError();
+  };
+  int block = 0;
+  int rc = tuned_block(ctx, key, (const void*)kern, run, &block);
+  if (rc != HISQ_OK) return rc;
+  HISQ_CUDA(run(block));
+  note_launch(ctx);
+  return HISQ_OK;
+}
+
+template <typename LR, typename SR, int EPI>
+static int launch_nr(hisq_ctx* ctx, const DslashKArgs& a, int nr) {
+  char key[64];
+  snprintf(key, sizeof key, "dslash/l%d/s%d/nr%d/e%d", Real<LR>::prec, Real<SR>::prec, nr, EPI);
+  switch (nr) {
+    case 1: return launch_group<LR, SR, 1, EPI>(ctx, a, key);
+    case 2: return launch_group<LR, SR, 2, EPI>(ctx, a, key);
+    case 4: return launch_group<LR, SR, 4, EPI>(ctx, a, key);
+    case 8: return launch_group<LR, SR, (sizeof(LR) == 8 ? 4 : 8), EPI>(ctx, a, key);
+    case 16: return launch_group<LR, SR, (sizeof(LR) == 8 ? 4 : 16), EPI>(ctx, a, key);
+  }
+  return set_error(HISQ_EINVAL, "unsupported rhs group %d", nr);
+}
+
+// Largest rhs group per launch: FP64 accumulators cap it at 4 (register budget).
+template <typename LR>
+static int max_group() {
+  return sizeof(LR) == 8 ? 4 : 16;
+}
+
+template <typename LR, typename SR>
+int dslash_launch_t(hisq_ctx* ctx, const DslashCall& c) {
+  const size_t site_bytes = 6 * sizeof(SR);
+  const int gmax = max_group<LR>();
+  int r0 = 0;
+  while (r0 < c.nrhs) {
+    const int left = c.nrhs - r0;
+    int nr = 1;
+    while (nr * 2 <= left && nr * 2 <= gmax) nr *= 2;
+    DslashKArgs a;
+    a.g = ctx->g;
+    a.links = ctx->links[Real<LR>::prec];
+    a.blk_bytes = link_block_bytes(Real<LR>::prec, ctx->g.half);
+    a.out_parity = c.out_parity;
+    a.out = (char*)c.out + (size_t)r0 * c.rhs_stride * site_bytes;
+    a.in = (const char*)c.in + (size_t)r0 * c.rhs_stride * site_bytes;
+    a.rhs_stride = c.rhs_stride;
+    a.y = c.y ? (const char*)c.y + (size_t)r0 * c.rhs_stride * site_bytes : nullptr;
+    for (int r = 0; r < 16; ++r) a.a[r] = (c.a_rhs && r0 + r < c.nrhs) ? c.a_rhs[r0 + r] : c.a;
+    a.partials = c.partials ? c.partials + (size_t)r0 * partial_stride(ctx) : nullptr;
+    a.dot_out = c.dot_out ? c.dot_out + r0 : nullptr;
+    a.counter = c.counter;
+    int rc = c.epi == EPI_PLAIN ? launch_nr<LR, SR, EPI_PLAIN>(ctx, a, nr) : launch_nr<LR, SR, EPI_AXPY>(ctx, a, nr);
+    if (rc != HISQ_OK) return rc;
+    r0 += nr;
+  }
+  return HISQ_OK;
+}
+
+}  // namespace hisq

@@ -1,0 +1,444 @@
+// Internal declarations of the HISQ GB300 library: context, precision traits, data
+// layout in HBM, device helpers shared by the kernels.
+//
+// Layout in HBM (per resident precision R, real type of that precision):
+//   links   one block per (parity p, kind k in {fat, long}, direction mu):
+//           block(p,k,mu) holds the folded link of every site of parity p (numbered cb),
+//           18 reals per link, split into "chunk planes" so that one thread loads one
+//           link with a few 16-byte coalesced loads:
+//             FP64      9 planes of double2          (1 complex entry each)
+//             FP32      4 planes of float4 + 1 float2 (2 complex entries per float4)
+//             FP16/BF16 2 planes of 16-byte vectors + 1 plane of 4 bytes (4 entries per 16 B)
+//           plane j of block b starts at block base + (sum of earlier chunk sizes) * (V/2).
+//   vectors the boundary layout [rhs][cb][color] of complex<R>, used unchanged inside.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/hisq.h"
+
+namespace hisq {
+
+// ------------------------------------------------------------------ complex arithmetic
+template <typename T>
+struct cplx {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ void cmac(cplx<T>& acc, const cplx<T>& a, const cplx<T>& b) {  // acc += a*b
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+template <typename T>
+__device__ __forceinline__ void cmac_conj(cplx<T>& acc, const cplx<T>& a, const cplx<T>& b) {  // acc += conj(a)*b
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+
+// ------------------------------------------------------------------ precision traits
+template <typename R>
+struct Real;
+template <>
+struct Real<double> {
+  using acc = double;
+  static constexpr int prec = HISQ_F64;
+};
+template <>
+struct Real<float> {
+  using acc = float;
+  static constexpr int prec = HISQ_F32;
+};
+template <>
+struct Real<__half> {
+  using acc = float;
+  static constexpr int prec = HISQ_F16;
+};
+template <>
+struct Real<__nv_bfloat16> {
+  using acc = float;
+  static constexpr int prec = HISQ_BF16;
+};
+
+__host__ __device__ inline size_t real_size(int prec) { return prec == HISQ_F64 ? 8 : prec == HISQ_F32 ? 4 : 2; }
+
+// ------------------------------------------------------------------ geometry
+struct Geom {
+  int L[4];
+  int stride[4];  // lexicographic strides 1, Lx, LxLy, LxLyLz
+  int half_x;     // Lx / 2
+  int half;       // V / 2 (sites per parity)
+  int V;
+};
+
+// Coordinates of the site numbered cb among the sites of parity p.
+__device__ __forceinline__ void site_coords(const Geom& g, int p, int cb, int c[4]) {
+  int xh = cb % g.half_x;
+  int rest = cb / g.half_x;
+  c[1] = rest % g.L[1];
+  rest /= g.L[1];
+  c[2] = rest % g.L[2];
+  c[3] = rest / g.L[2];
+  c[0] = 2 * xh + ((p + c[1] + c[2] + c[3]) & 1);
+}
+
+__device__ __forceinline__ int lex_index(const Geom& g, const int c[4]) {
+  return c[0] + g.stride[1] * c[1] + g.stride[2] * c[2] + g.stride[3] * c[3];
+}
+
+// cb number of the neighbour of site (c, idx) at offset k (|k| < L) along mu.
+__device__ __forceinline__ int neighbour_cb(const Geom& g, const int c[4], int idx, int mu, int k) {
+  int cm = c[mu] + k;
+  int n = idx + k * g.stride[mu];
+  if (cm >= g.L[mu]) n -= g.L[mu] * g.stride[mu];
+  if (cm < 0) n += g.L[mu] * g.stride[mu];
+  return n >> 1;
+}
+
+// ------------------------------------------------------------------ link access
+// Bytes of one link block (all sites of one parity, one kind, one direction).
+__host__ __device__ inline size_t link_block_bytes(int prec, int half) { return (size_t)half * 18 * real_size(prec); }
+
+__device__ __forceinline__ double2 ld_stream(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned ld_stream(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+template <typename R>
+__device__ __forceinline__ cplx<float> unpack2(unsigned w);
+template <>
+__device__ __forceinline__ cplx<float> unpack2<__half>(unsigned w) {
+  __half2 h = *reinterpret_cast<__half2*>(&w);
+  float2 f = __half22float2(h);
+  return {f.x, f.y};
+}
+template <>
+__device__ __forceinline__ cplx<float> unpack2<__nv_bfloat16>(unsigned w) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+  float2 f = __bfloat1622float2(h);
+  return {f.x, f.y};
+}
+
+// Load the 3x3 link of site cb from a link block (row-major entries U[3*row+col]).
+template <typename R>
+struct LinkIO;
+
+template <>
+struct LinkIO<double> {
+  __device__ __forceinline__ static void load(const char* blk, int half, int cb, cplx<double> U[9]) {
+    const double2* p = reinterpret_cast<const double2*>(blk);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 v = ld_stream(p + (size_t)k * half + cb);
+      U[k] = {v.x, v.y};
+    }
+  }
+  __device__ __forceinline__ static void store(char* blk, int half, int cb, const cplx<double> U[9]) {
+    double2* p = reinterpret_cast<double2*>(blk);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) p[(size_t)k * half + cb] = make_double2(U[k].re, U[k].im);
+  }
+};
+
+template <>
+struct LinkIO<float> {
+  __device__ __forceinline__ static void load(const char* blk, int half, int cb, cplx<float> U[9]) {
+    const float4* p = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float4 v = ld_stream(p + (size_t)j * half + cb);
+      U[2 * j] = {v.x, v.y};
+      U[2 * j + 1] = {v.z, v.w};
+    }
+    const float2* q = reinterpret_cast<const float2*>(blk + (size_t)64 * half);
+    float2 v = ld_stream(q + cb);
+    U[8] = {v.x, v.y};
+  }
+  __device__ __forceinline__ static void store(char* blk, int half, int cb, const cplx<double> U[9]) {
+    float4* p = reinterpret_cast<float4*>(blk);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      p[(size_t)j * half + cb] = make_float4((float)U[2 * j].re, (float)U[2 * j].im, (float)U[2 * j + 1].re,
+                                             (float)U[2 * j + 1].im);
+    float2* q = reinterpret_cast<float2*>(blk + (size_t)64 * half);
+    q[cb] = make_float2((float)U[8].re, (float)U[8].im);
+  }
+};
+
+template <typename H>
+struct LinkIO16 {
+  __device__ __forceinline__ static void load(const char* blk, int half, int cb, cplx<float> U[9]) {
+    const uint4* p = reinterpret_cast<const uint4*>(blk);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint4 v = ld_stream(p + (size_t)j * half + cb);
+      U[4 * j + 0] = unpack2<H>(v.x);
+      U[4 * j + 1] = unpack2<H>(v.y);
+      U[4 * j + 2] = unpack2<H>(v.z);
+      U[4 * j + 3] = unpack2<H>(v.w);
+    }
+    const unsigned* q = reinterpret_cast<const unsigned*>(blk + (size_t)32 * half);
+    U[8] = unpack2<H>(ld_stream(q + cb));
+  }
+  __device__ __forceinline__ static unsigned pack(double re, double im);
+  __device__ __forceinline__ static void store(char* blk, int half, int cb, const cplx<double> U[9]) {
+    uint4* p = reinterpret_cast<uint4*>(blk);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint4 v;
+      v.x = pack(U[4 * j].re, U[4 * j].im);
+      v.y = pack(U[4 * j + 1].re, U[4 * j + 1].im);
+      v.z = pack(U[4 * j + 2].re, U[4 * j + 2].im);
+      v.w = pack(U[4 * j + 3].re, U[4 * j + 3].im);
+      p[(size_t)j * half + cb] = v;
+    }
+    unsigned* q = reinterpret_cast<unsigned*>(blk + (size_t)32 * half);
+    q[cb] = pack(U[8].re, U[8].im);
+  }
+};
+template <>
+__device__ __forceinline__ unsigned LinkIO16<__half>::pack(double re, double im) {
+  // double -> half directly (one rounding), round to nearest even
+  __half2 h = __halves2half2(__double2half(re), __double2half(im));
+  return *reinterpret_cast<unsigned*>(&h);
+}
+template <>
+__device__ __forceinline__ unsigned LinkIO16<__nv_bfloat16>::pack(double re, double im) {
+  __nv_bfloat162 h = __halves2bfloat162(__double2bfloat16(re), __double2bfloat16(im));
+  return *reinterpret_cast<unsigned*>(&h);
+}
+template <>
+struct LinkIO<__half> : LinkIO16<__half> {};
+template <>
+struct LinkIO<__nv_bfloat16> : LinkIO16<__nv_bfloat16> {};
+
+// ------------------------------------------------------------------ vector access ([cb][3] complex<R>)
+template <typename R>
+struct VecIO;
+template <>
+struct VecIO<double> {
+  __device__ __forceinline__ static void load(const void* v, size_t site, cplx<double> o[3]) {
+    const double2* p = reinterpret_cast<const double2*>(v) + 3 * site;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double2 w = p[c];
+      o[c] = {w.x, w.y};
+    }
+  }
+  __device__ __forceinline__ static void store(void* v, size_t site, const cplx<double> o[3]) {
+    double2* p = reinterpret_cast<double2*>(v) + 3 * site;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c] = make_double2(o[c].re, o[c].im);
+  }
+};
+template <>
+struct VecIO<float> {
+  __device__ __forceinline__ static void load(const void* v, size_t site, cplx<float> o[3]) {
+    const float2* p = reinterpret_cast<const float2*>(v) + 3 * site;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 w = p[c];
+      o[c] = {w.x, w.y};
+    }
+  }
+  __device__ __forceinline__ static void store(void* v, size_t site, const cplx<float> o[3]) {
+    float2* p = reinterpret_cast<float2*>(v) + 3 * site;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c] = make_float2(o[c].re, o[c].im);
+  }
+};
+template <>
+struct VecIO<__half> {
+  __device__ __forceinline__ static void load(const void* v, size_t site, cplx<float> o[3]) {
+    const __half2* p = reinterpret_cast<const __half2*>(v) + 3 * site;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 f = __half22float2(p[c]);
+      o[c] = {f.x, f.y};
+    }
+  }
+  __device__ __forceinline__ static void store(void* v, size_t site, const cplx<float> o[3]) {
+    __half2* p = reinterpret_cast<__half2*>(v) + 3 * site;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c] = __floats2half2_rn(o[c].re, o[c].im);
+  }
+};
+template <>
+struct VecIO<__nv_bfloat16> {
+  __device__ __forceinline__ static void load(const void* v, size_t site, cplx<float> o[3]) {
+    const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(v) + 3 * site;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 f = __bfloat1622float2(p[c]);
+      o[c] = {f.x, f.y};
+    }
+  }
+  __device__ __forceinline__ static void store(void* v, size_t site, const cplx<float> o[3]) {
+    __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(v) + 3 * site;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c] = __floats2bfloat162_rn(o[c].re, o[c].im);
+  }
+};
+
+// ------------------------------------------------------------------ reductions
+// Sum of a double over the block (blockDim.x a multiple of 32, <= 1024); thread 0 gets
+// the result. Fixed order, so the sum is deterministic for a fixed launch shape.
+__device__ __forceinline__ double block_sum_dyn(double v, double* smem /* 32 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) smem[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int k = 0; k < nw; ++k) s += smem[k];
+  }
+  __syncthreads();
+  return s;
+}
+
+// Marks this block done; returns true in every thread of the last block to finish.
+// Partials written before the call are visible to the last block. The counter is
+// reset by the last block so the next launch starts from zero.
+__device__ __forceinline__ bool last_block_done(unsigned* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    is_last = (prev == gridDim.x * gridDim.y * gridDim.z - 1);
+  }
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+  return is_last;
+}
+
+// Deterministic sum of partials[0..n) by the (single) finishing block; thread 0 gets it.
+__device__ __forceinline__ double sum_partials_dyn(const double* partials, int n, double* smem) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(partials + i);
+  return block_sum_dyn(s, smem);
+}
+
+}  // namespace hisq
+
+// ------------------------------------------------------------------ context (host side)
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct hisq_ctx {
+  hisq::Geom g;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  unsigned prec_mask = 0;
+  char* links[4] = {nullptr, nullptr, nullptr, nullptr};  // per precision, 16 blocks each
+  std::vector<unsigned char> t_loaded;                    // per t-slice
+  unsigned load_flags = 0;
+  bool links_ready = false;
+  int num_sms = 0;
+  int autotune = 1;
+  std::map<std::string, DevBuf> ws;  // named device workspaces
+  std::map<std::string, int> tune;   // kernel key -> block size
+  void* pinned = nullptr;            // small pinned host buffer for scalar read-back
+  unsigned* d_counters = nullptr;    // last-block counters (zeroed), 64 entries
+  int* d_flag = nullptr;             // device error flag
+  long long launches = 0;            // kernels executed (eager + graph nodes)
+  bool capturing = false;            // inside this library's own stream capture
+};
+
+namespace hisq {
+
+// Error state of the calling thread.
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+#define HISQ_CUDA(call)                                        \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return hisq::cuda_error(_e, #call); \
+  } while (0)
+
+void* workspace(hisq_ctx* ctx, const char* name, size_t bytes);  // nullptr on failure
+
+// Count one eager kernel launch (launches recorded into a graph are counted per replay).
+inline void note_launch(hisq_ctx* ctx, int n = 1) {
+  if (!ctx->capturing) ctx->launches += n;
+}
+
+inline const char* link_block(const hisq_ctx* ctx, int prec, int parity, int kind, int mu) {
+  return ctx->links[prec] + (size_t)((parity * 2 + kind) * 4 + mu) * link_block_bytes(prec, ctx->g.half);
+}
+
+// ------------------------------------------------------------------ Dslash launcher interface
+// Epilogues of the Dslash kernel:
+//   EPI_PLAIN   out = D in
+//   EPI_AXPY    out = a * y - D in  and (optionally) dot[r] += Re<y_r, out_r> in FP64,
+//               with a = 4 m^2 + sigma: the second half of A y = (4m^2+sigma) y - D_eo D_oe y.
+enum { EPI_PLAIN = 0, EPI_AXPY = 1 };
+
+struct DslashCall {
+  int out_parity;
+  void* out;
+  const void* in;
+  int nrhs;
+  size_t rhs_stride;  // sites between consecutive rhs vectors (normally V/2)
+  // EPI_AXPY
+  const void* y = nullptr;
+  double a = 0.0;
+  const double* a_rhs = nullptr;  // host array [nrhs]: per-rhs coefficient (overrides a)
+  double* partials = nullptr;  // [nrhs][grid] when non-null: reduce Re<y, out>
+  double* dot_out = nullptr;   // [nrhs] final sums (written by the last block)
+  unsigned* counter = nullptr;
+  int epi = EPI_PLAIN;
+};
+
+// Launch D (link precision lp, spinor precision sp) on ctx->stream.
+int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& call);
+int dslash_grid(hisq_ctx* ctx, int lp, int sp, int nrhs, int epi, int* block_out);  // grid size used
+double dslash_bytes(const hisq_ctx* ctx, int lp, int sp, int nrhs);
+
+// Link packing (fold phases and boundary, convert to every resident precision).
+int pack_links_slab(hisq_ctx* ctx, const double* d_fat, const double* d_long, int t0, int nt, unsigned flags);
+
+}  // namespace hisq

@@ -1,0 +1,69 @@
+// Launch autotuner: the first launch of a kernel under a given key (kernel, precisions,
+// rhs group, epilogue; the context fixes the lattice) times each candidate block size
+// with CUDA events on the context's stream and keeps the fastest. Only idempotent
+// kernels are tuned this way (the Dslash family: out = f(in) with no read of out).
+// Inside a stream capture nothing is timed: an untuned key falls back to 256 threads.
+#pragma once
+#include <stdio.h>
+
+#include "internal.cuh"
+
+namespace hisq {
+
+// Grid cap for grid-stride kernels: two waves of a fully occupied GPU.
+inline int max_grid_blocks(const hisq_ctx* ctx, int block) { return ctx->num_sms * (2048 / block) * 2; }
+// Room per rhs in reduction-partials buffers (covers the smallest tuned block, 64).
+inline size_t partial_stride(const hisq_ctx* ctx) { return (size_t)ctx->num_sms * 64; }
+
+template <typename Run>
+int tuned_block(hisq_ctx* ctx, const char* key, const void* func, Run run, int* block_out) {
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) {
+    *block_out = it->second;
+    return HISQ_OK;
+  }
+  cudaFuncAttributes fa;
+  HISQ_CUDA(cudaFuncGetAttributes(&fa, func));
+  const int limit = fa.maxThreadsPerBlock;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  HISQ_CUDA(cudaStreamIsCapturing(ctx->stream, &cap));
+  if (!ctx->autotune || cap != cudaStreamCaptureStatusNone) {
+    int b = limit >= 256 ? 256 : 128;
+    *block_out = b;
+    if (cap == cudaStreamCaptureStatusNone) ctx->tune[key] = b;
+    return HISQ_OK;
+  }
+  static const int cands[] = {64, 128, 256, 512};
+  cudaEvent_t e0, e1;
+  HISQ_CUDA(cudaEventCreate(&e0));
+  HISQ_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_b = 128;
+  for (int b : cands) {
+    if (b > limit) continue;
+    cudaError_t err = run(b);  // warm-up
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < 3; ++r) run(b);
+    note_launch(ctx, 4);
+    cudaEventRecord(e1, ctx->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_b = b;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HISQ_CUDA(cudaGetLastError());
+  ctx->tune[key] = best_b;
+  *block_out = best_b;
+  return HISQ_OK;
+}
+
+}  // namespace hisq

@@ -17,3 +17,15 @@ def pytest_configure(config):
 def rng():
     import numpy as np
     return np.random.default_rng(12345)
+
+
+@pytest.fixture(scope="session")
+def hisq():
+    """The CUDA library, built in-tree if stale. Fails (no fallback) when it cannot be built or loaded."""
+    import torch
+    from paper_2111_10354_gb300 import build
+    build.build()
+    import paper_2111_10354_gb300 as h
+    h.lib()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return h
