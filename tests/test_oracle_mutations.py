@@ -1,0 +1,74 @@
+"""The oracle's pins bite: each plausible mistake, planted in a scratch copy of the oracle (CPU only),
+makes the pin tests fail. The real oracle is untouched."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("backward hop without complex conjugate", "a += conj(U[3 * j + i]) * v[j];", "a += U[3 * j + i] * v[j];"),
+    ("backward hop without transpose", "a += conj(U[3 * j + i]) * v[j];", "a += conj(U[3 * i + j]) * v[j];"),
+    ("forward link transposed", "a += U[3 * i + j] * v[j];", "a += U[3 * j + i] * v[j];"),
+    ("staggered phase over one direction too many", "for (int nu = 0; nu < mu; ++nu) sum += c[nu];",
+     "for (int nu = 0; nu <= mu; ++nu) sum += c[nu];"),
+    ("long-link boundary sign on two slices only", "if (c[3] >= L[3] - 3) sl = -sl;", "if (c[3] >= L[3] - 2) sl = -sl;"),
+    ("fat-link boundary sign dropped", "if (c[3] == L[3] - 1) sf = -sf;", "if (c[3] == L[3] - 99) sf = -sf;"),
+    ("Naik backward hop of two sites", "shifted(L, c, mu, -3)", "shifted(L, c, mu, -2)"),
+    ("backward link taken at the output site", "add_dag_mat_vec(out, link_at(fat, bwd1, mu), chi_at(ctx, bwd1), -1.0);",
+     "add_dag_mat_vec(out, link_at(fat, idx, mu), chi_at(ctx, bwd1), -1.0);"),
+    ("sign of D_eo D_oe in A", "y[i] = (4.0 * mass * mass + sigma) * x[i] - dd[i];",
+     "y[i] = (4.0 * mass * mass + sigma) * x[i] + dd[i];"),
+    ("mass term 2m instead of 4m^2", "y[i] = (4.0 * mass * mass + sigma) * x[i] - dd[i];",
+     "y[i] = (2.0 * mass + sigma) * x[i] - dd[i];"),
+    ("terms assigned instead of accumulated", "out[i] += s * a;", "out[i] = s * a;"),
+    ("CG beta inverted", "double beta = rr_new / rr;", "double beta = rr / rr_new;"),
+    ("multi-shift zeta without the shift difference", "(1.0 + dk * alpha)", "(1.0 + alpha)"),
+]
+
+
+@pytest.fixture(scope="module")
+def scratch(tmp_path_factory):
+    d = tmp_path_factory.mktemp("oracle_mutant")
+    for sub in ("oracle", "hisq_inputs"):
+        shutil.copytree(os.path.join(ROOT, sub), os.path.join(d, sub),
+                        ignore=shutil.ignore_patterns("liboracle.so", "__pycache__", "*.tmp*"))
+    os.makedirs(os.path.join(d, "tests"))
+    for f in ("conftest.py", "test_oracle_dslash.py", "test_oracle_solvers.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(d, "tests", f))
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(d, "tests", "golden"))
+    return str(d)
+
+
+def run_pins(d):
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "tests"], cwd=d,
+                         capture_output=True, text=True, timeout=600)
+    return res.returncode, res.stdout[-400:]
+
+
+def test_unmutated_copy_passes(scratch):
+    rc, out = run_pins(scratch)
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_mutation_is_caught(scratch, name, old, new):
+    src_path = os.path.join(scratch, "oracle", "oracle.c")
+    original = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert old in original, "mutation anchor missing: " + old
+    with open(src_path, "w") as f:
+        f.write(original.replace(old, new, 1))
+    lib = os.path.join(scratch, "oracle", "liboracle.so")
+    if os.path.exists(lib):
+        os.remove(lib)
+    try:
+        rc, out = run_pins(scratch)
+        assert rc != 0, "pins did not catch: " + name
+    finally:
+        with open(src_path, "w") as f:
+            f.write(original)
+        if os.path.exists(lib):
+            os.remove(lib)
