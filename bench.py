@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the steps only: no e2e, comparison solves or CPU baseline (for profiler launch lists)")
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
+    ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned"],
+                    help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
     return ap.parse_args()
 
 
@@ -197,6 +199,18 @@ def workload_name():
     return "HISQ mixed-precision CG to 1e-10 on 48^3x12 (FP32 inner D_eo/D_oe, FP64 reliable updates every 50), m=0.01"
 
 
+def aggregate(t_local, bytes_local, dist, device):
+    """Whole-job figures of N replicas: the slowest rank's time and the bytes of all ranks."""
+    if dist is None:
+        return float(t_local), float(bytes_local)
+    import torch
+    tt = torch.tensor([float(t_local)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    bb = torch.tensor([float(bytes_local)], device=device, dtype=torch.float64)
+    dist.all_reduce(bb)
+    return float(tt.item()), float(bb.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def vec_like(torch, half, prec, nrhs=1, seed=5):
     import hisq_inputs as hin
@@ -278,15 +292,7 @@ def run_ours(args, rank, world, local):
         e1.synchronize()
         barrier()
     t_ms = e0.elapsed_time(e1)
-    t_max = t_ms
-    tot_bytes = dbytes
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        bb = torch.tensor([dbytes], device="cuda", dtype=torch.float64)
-        dist.all_reduce(bb)
-        tot_bytes = float(bb.item())
+    t_max, tot_bytes = aggregate(t_ms, dbytes, dist, "cuda")
     value = tot_bytes / (t_max * 1e-3) / 1e9
     worst_res = max(r for _, _, r in iters)
 
@@ -312,13 +318,7 @@ def run_ours(args, rank, world, local):
         e2e_bytes += st["dslash_bytes"]
     barrier()
     t_e2e = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-        bb = torch.tensor([e2e_bytes], device="cuda", dtype=torch.float64)
-        dist.all_reduce(bb)
-        e2e_bytes = float(bb.item())
+    t_e2e, e2e_bytes = aggregate(t_e2e, e2e_bytes, dist, "cuda")
     vec_bytes = b_host.nbytes
 
     # roofline of the dominant kernel: the FP32 Dslash, timed live on its stream
@@ -415,6 +415,176 @@ def run_sweep():
         torch.cuda.empty_cache()
 
 
+# ----------------------------------------------------------------------------- other workloads
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, out
+
+
+def row_multirhs(h, torch, hin):
+    """48^3x12, FP32 storage: Dslash and mixed CG with 1, 4, 8, 16 sources per link read."""
+    L = (48, 48, 48, 12)
+    fat, lng = hin.gen_links(L, 1002, 0.3, 0.1)
+    stream = torch.cuda.Stream()
+    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=stream).load(fat, lng)
+    peak, _ = peaks()
+    for n in (1, 4, 8, 16):
+        ms = time_dslash(torch, lat, h.HISQ_F32, n, 20, stream)
+        by = lat.dslash_bytes(h.HISQ_F32, n)
+        b = torch.from_numpy(hin.gen_source(2002, lat.half, n)).cuda()
+        x = torch.zeros_like(b)
+        lat.cg(x, b, 0.01, 1e-10, 5000, nrhs=n, inner_prec=h.HISQ_F32)  # warm-up / tuning
+        x.zero_()
+        dt, (rc, st) = _timed(torch, lambda: lat.cg(x, b, 0.01, 1e-10, 5000, nrhs=n, inner_prec=h.HISQ_F32))
+        print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": "f32", "nrhs": n,
+                          "dslash_us": round(ms * 1e3, 1), "dslash_GBps": round(by / ms / 1e6, 1),
+                          "dslash_frac_hbm": round(by / ms / 1e6 / peak, 3),
+                          "dslash_GFLOPs": round(1146 * n * lat.half / (ms * 1e-3) / 1e9, 1),
+                          "cg_s": round(dt, 4), "cg_s_per_rhs": round(dt / n, 4), "cg_iters": st["iters"],
+                          "worst_true_res": st["true_rel_residual"]}), flush=True)
+
+
+def row_multishift(h, torch, hin):
+    """48^3x12, m = 0.0025, 14 shifts log-spaced in [1e-5, 1], every shift to 1e-9."""
+    L = (48, 48, 48, 12)
+    fat, lng = hin.gen_links(L, 1002, 0.3, 0.1)
+    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=torch.cuda.Stream()).load(fat, lng)
+    shifts = np.logspace(-5, 0, 14)
+    b = torch.from_numpy(hin.gen_source(2002, lat.half, 1)).cuda()
+    x = torch.zeros((14, lat.half, 3), dtype=torch.complex128, device="cuda")
+    for name, prec in (("fp32_krylov+refine", h.HISQ_F32), ("fp64", h.HISQ_F64)):
+        lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 20000, inner_prec=prec)
+        dt, (rc, st) = _timed(torch, lambda: lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 20000, inner_prec=prec))
+        print(json.dumps({"row": "multishift", "variant": name, "s": round(dt, 4), "iters": st["iters"],
+                          "shift_iters": st["shift_iters"], "max_true_res": max(st["shift_residual"]),
+                          "converged": st["converged"], "kernel_launches": st["kernel_launches"]}), flush=True)
+    # reference point: 14 independent mixed-precision solves
+    xs = torch.zeros((1, lat.half, 3), dtype=torch.complex128, device="cuda")
+    t = 0.0
+    for s_ in shifts:
+        xs.zero_()
+        dt, _ = _timed(torch, lambda: h.hisq_cg(lat.ctx, xs, b, 1, float(np.sqrt(0.0025 ** 2 + s_ / 4)), 1e-9,
+                                                20000, h.make_opts(inner_prec=h.HISQ_F32)))
+        t += dt
+    print(json.dumps({"row": "multishift", "variant": "14 separate mixed CG", "s": round(t, 4)}), flush=True)
+
+
+def row_batch(h, torch, hin):
+    """64 lattices (32 x 16^4, 19 x 24^3x8, 13 x 32^3x8), per-lattice eps and mass, to 1e-10."""
+    mix = hin.lattice_mix_64()
+    batch = h.Batch([m["dims"] for m in mix], stream=torch.cuda.Stream())
+    lats, bs = [], []
+    for l, m in enumerate(mix):
+        fat, lng = hin.gen_links(m["dims"], m["gauge_seed"], m["eps"], 0.1)
+        batch.load(l, fat, lng)
+        lats.append((fat, lng))
+        bs.append(hin.gen_source(m["source_seed"], int(np.prod(m["dims"])) // 2, 1)[0])
+    b = torch.from_numpy(np.concatenate([v.reshape(-1) for v in bs]).reshape(-1, 3)).cuda()
+    masses = [m["mass"] for m in mix]
+    x = torch.zeros_like(b)
+    for name, prec in (("batched mixed f32/f64", h.HISQ_F32), ("batched fp64", h.HISQ_F64)):
+        batch.cg(x, b, masses, 1e-10, 10000, inner_prec=prec)
+        x.zero_()
+        dt, (rc, st) = _timed(torch, lambda: batch.cg(x, b, masses, 1e-10, 10000, inner_prec=prec))
+        print(json.dumps({"row": "batch", "variant": name, "lattices": 64, "s": round(dt, 4),
+                          "max_iters": st["iters"], "cycles": st["reliable_updates"],
+                          "max_true_res": max(st["lattice_residual"]), "converged": st["converged"],
+                          "kernel_launches": st["kernel_launches"],
+                          "dslash_GBps_whole_solve": round(st["dslash_bytes"] / dt / 1e9, 1)}), flush=True)
+    # reference point: the same 64 solves one lattice at a time through hisq_cg
+    t = 0.0
+    for l, m in enumerate(mix):
+        lat = h.Lattice(m["dims"], precs=(h.HISQ_F64, h.HISQ_F32)).load(*lats[l])
+        bl = torch.from_numpy(bs[l]).reshape(1, -1, 3).cuda()
+        xl = torch.zeros_like(bl)
+        lat.cg(xl, bl, m["mass"], 1e-10, 10000, inner_prec=h.HISQ_F32)
+        xl.zero_()
+        dt, _ = _timed(torch, lambda: lat.cg(xl, bl, m["mass"], 1e-10, 10000, inner_prec=h.HISQ_F32))
+        t += dt
+        lat.close()
+    print(json.dumps({"row": "batch", "variant": "64 sequential single-lattice mixed CG", "s": round(t, 4)}),
+          flush=True)
+
+
+def row_learned(h, torch, hin, epochs=6, batch_pairs=16):
+    """32^3x8, m = 0.001, eps = 0.35: train the PTC net on 4 fields x 128 (source, solution) pairs,
+    then flexible CG with it vs mixed-precision CG on 4 held-out fields, to 1e-10."""
+    import oracle.ptc as optc
+    L = (32, 32, 32, 8)
+    mass = 0.001
+    stream = torch.cuda.Stream()
+
+    def field(seed):
+        fat, lng = hin.gen_links(L, seed, 0.35, 0.1)
+        return h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=stream).load(fat, lng)
+
+    train = [field(4000 + i) for i in range(4)]
+    half = train[0].half
+    t0 = time.perf_counter()
+    pairs = []
+    for i, lat in enumerate(train):
+        b = torch.from_numpy(hin.gen_source(5000 + i, half, 128)).cuda()
+        x = torch.zeros_like(b)
+        for k in range(0, 128, 16):  # 16 sources per link read
+            lat.cg(x[k:k + 16], b[k:k + 16], mass, 1e-10, 20000, nrhs=16, inner_prec=h.HISQ_F32)
+        pairs.append((b.to(torch.complex64), x.to(torch.complex64)))
+    t_data = time.perf_counter() - t0
+    W1, W2 = optc.init_weights(4000, scale=0.05)
+    W1[0, 0, 0] = W2[0, 0, 0] = 1.0
+    net = h.Ptc(train[0])
+    net.set_weights(W1, W2)
+    t0 = time.perf_counter()
+    losses = []
+    for ep in range(epochs):
+        ep_loss = []
+        for k in range(0, 128, batch_pairs):
+            for i, lat in enumerate(train):
+                net.bind(lat)
+                b, x = pairs[i]
+                loss, _, _ = net.train_step(b[k:k + batch_pairs].contiguous(), x[k:k + batch_pairs].contiguous(),
+                                            batch_pairs, 0.01)
+                ep_loss.append(loss)
+        losses.append(float(np.mean(ep_loss)))
+    t_train = time.perf_counter() - t0
+    print(json.dumps({"row": "learned", "phase": "train", "pairs": 512, "epochs": epochs,
+                      "data_s": round(t_data, 2), "train_s": round(t_train, 2), "loss_per_epoch": losses}),
+          flush=True)
+    for i in range(4):
+        lat = field(4100 + i)
+        net.bind(lat)
+        b = torch.from_numpy(hin.gen_source(6000 + i, half, 1)).cuda()
+        x = torch.zeros_like(b)
+        net.fcg(x, b, mass, 1e-10, 20000)
+        x.zero_()
+        dt_f, (rc_f, st_f) = _timed(torch, lambda: net.fcg(x, b, mass, 1e-10, 20000))
+        x2 = torch.zeros_like(b)
+        lat.cg(x2, b, mass, 1e-10, 20000, inner_prec=h.HISQ_F32)
+        x2.zero_()
+        dt_c, (rc_c, st_c) = _timed(torch, lambda: lat.cg(x2, b, mass, 1e-10, 20000, inner_prec=h.HISQ_F32))
+        x3 = torch.zeros_like(b)
+        dt_d, (rc_d, st_d) = _timed(torch, lambda: lat.cg(x3, b, mass, 1e-10, 20000, inner_prec=h.HISQ_F64))
+        print(json.dumps({"row": "learned", "phase": "held-out", "field": 4100 + i,
+                          "fcg": {"s": round(dt_f, 4), "iters": st_f["iters"], "true_res": st_f["true_rel_residual"]},
+                          "mixed_cg": {"s": round(dt_c, 4), "iters": st_c["iters"],
+                                       "true_res": st_c["true_rel_residual"]},
+                          "fp64_cg": {"s": round(dt_d, 4), "iters": st_d["iters"],
+                                      "true_res": st_d["true_rel_residual"]}}), flush=True)
+
+
+def run_row(name):
+    import torch
+
+    import __graft_entry__
+    import hisq_inputs as hin
+    __graft_entry__.build()
+    import paper_2111_10354_gb300 as h
+    {"multirhs": row_multirhs, "multishift": row_multishift, "batch": row_batch,
+     "learned": row_learned}[name](h, torch, hin)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -422,6 +592,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.sweep:
         run_sweep()
+        return
+    if args.row:
+        run_row(args.row)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

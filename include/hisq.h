@@ -174,6 +174,77 @@ int hisq_multishift_cg(hisq_ctx* ctx, double* x, const double* b, int nshift, co
                        double mass, const double* rel_tol, int maxiter, const hisq_solver_opts* opts,
                        hisq_solver_stats* stats);
 
+/* ---------------------------------------------------------------- batches of lattices */
+/*
+ * A batch of independent lattices of (possibly) different sizes, solved together: every
+ * step of the batched CG is one persistent launch over a tile table that covers all
+ * lattices, and one CUDA graph holds a whole reliable cycle (inner iterations, fold, FP64
+ * residual, reliable update). This is the many-small-lattices form of the paper's CG
+ * (Sec. 2, Sec. 3); the paper itself batches right-hand sides, not lattices.
+ * dims: nlat x 4 extents (each even and >= 4), nlat <= 256. FP64 and FP32 links are always
+ * resident. Vectors of the batch: the even-site vectors of all lattices back to back,
+ * complex128 [lattice][V_l/2][3]; hisq_batch_vector_offset gives lattice l's first complex
+ * entry (l = nlat gives the total).
+ */
+typedef struct hisq_batch hisq_batch;
+int hisq_batch_create(hisq_batch** out, int nlat, const int* dims, unsigned prec_mask, void* stream);
+int hisq_batch_destroy(hisq_batch* batch);
+/* Links of one lattice of the batch, as hisq_load_links. */
+int hisq_batch_load_links(hisq_batch* batch, int lattice, const double* fat, const double* lng, unsigned flags);
+long long hisq_batch_vector_offset(const hisq_batch* batch, int lattice);
+long long hisq_batch_launch_count(const hisq_batch* batch);
+/*
+ * Solve A_l x_l = b_l (A_l = 4 m_l^2 - D_eo D_oe on lattice l) for every lattice to
+ * ||b_l - A_l x_l|| <= rel_tol ||b_l||, verified in FP64. mass: nlat masses. opts->inner_prec
+ * HISQ_F32 (mixed precision, FP64 reliable updates every reliable_period iterations) or
+ * HISQ_F64. x: initial guess in, solution out; host or device. iters, true_res: optional
+ * per-lattice outputs [nlat]. stats: aggregate (iters = the largest per-lattice count).
+ */
+int hisq_batch_cg(hisq_batch* batch, double* x, const double* b, const double* mass, double rel_tol, int maxiter,
+                  const hisq_solver_opts* opts, hisq_solver_stats* stats, int* iters, double* true_res);
+
+/* ---------------------------------------------------------------- learned preconditioner */
+/*
+ * A gauge-equivariant parallel-transport convolution (PTC) network used as the
+ * preconditioner of a flexible CG (the project's extension of the paper's CG; the paper
+ * has none). Layer: psi'_a(x) = sum_b sum_h W[a][b][h] (T_h psi_b)(x) over 9 hops
+ * h = 0, +x, +y, +z, +t, -x, -y, -z, -t, with T_+mu psi(x) = F_mu(x) psi(x+mu) and
+ * T_-mu psi(x) = F_mu(x-mu)^dag psi(x-mu) through the context's folded FP32 fat links.
+ * Network: 1 -> channels -> 1 (channels = 8), linear; input an even-site vector embedded
+ * with zeros on odd sites, output restricted to even sites. Channel mixing runs on the
+ * tensor cores in BF16 with FP32 accumulation; master weights are FP32.
+ * Weights: w1 [channels][1][9], w2 [1][channels][9], complex as (re, im) float pairs.
+ * Network vectors: device, complex64 [nvec][V/2][3] (even sites).
+ */
+typedef struct hisq_ptc hisq_ptc;
+int hisq_ptc_create(hisq_ptc** out, hisq_ctx* ctx, int channels);
+/* Frees the network's buffers only; valid before or after its context is destroyed. */
+int hisq_ptc_destroy(hisq_ptc* ptc);
+/* Host or device FP32 weights in; resets the Adam moments. */
+int hisq_ptc_set_weights(hisq_ptc* ptc, const float* w1, const float* w2);
+int hisq_ptc_get_weights(hisq_ptc* ptc, float* w1, float* w2);
+/* Rebind the network (weights and Adam moments kept) to another context of the same lattice
+ * shape, e.g. to train on several gauge fields. */
+int hisq_ptc_bind(hisq_ptc* ptc, hisq_ctx* ctx);
+/* z = N(r) for nvec vectors (device). HISQ_ETIMEOUT if a tensor-core completion wait ran out. */
+int hisq_ptc_apply(hisq_ptc* ptc, float* z, const float* r, int nvec);
+/*
+ * Loss = mean over npairs of |N(b_i) - x_i|^2 / |x_i|^2 and its gradients with respect to
+ * conj(w1), conj(w2) (loss, g1, g2: optional host outputs); with lr > 0 one Adam step on the
+ * FP32 master weights follows. b, x: device complex64 [npairs][V/2][3].
+ */
+int hisq_ptc_train_step(hisq_ptc* ptc, const float* b, const float* x, int npairs, float lr, float* loss, float* g1,
+                        float* g2);
+/*
+ * Flexible CG (truncated to one previous direction, Notay 2000) preconditioned by the network:
+ * z = N(r); p = z - (<q_old, z>/<q_old, p_old>) p_old; alpha = <p, r>/<p, A p> (complex in
+ * general). Inner vectors FP32 with FP32 links, FP64 reductions and solution, FP64 reliable
+ * update (true residual, restart p = N(r)) every opts->reliable_period iterations. Same
+ * conventions and errors as hisq_cg (single rhs).
+ */
+int hisq_fcg(hisq_ctx* ctx, hisq_ptc* ptc, double* x, const double* b, double mass, double rel_tol, int maxiter,
+             const hisq_solver_opts* opts, hisq_solver_stats* stats);
+
 /* ---------------------------------------------------------------- diagnostics */
 const char* hisq_strerror(int code);
 const char* hisq_last_error(void);

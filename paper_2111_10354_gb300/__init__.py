@@ -96,6 +96,25 @@ def _load():
     lib.hisq_launch_count.argtypes = [vp]
     lib.hisq_launch_count.restype = ctypes.c_longlong
     lib.hisq_tune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.hisq_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(ctypes.c_int), ctypes.c_uint, vp]
+    lib.hisq_batch_destroy.argtypes = [vp]
+    lib.hisq_batch_load_links.argtypes = [vp, ip, vp, vp, ctypes.c_uint]
+    lib.hisq_batch_vector_offset.argtypes = [vp, ip]
+    lib.hisq_batch_vector_offset.restype = ctypes.c_longlong
+    lib.hisq_batch_launch_count.argtypes = [vp]
+    lib.hisq_batch_launch_count.restype = ctypes.c_longlong
+    lib.hisq_batch_cg.argtypes = [vp, vp, vp, vp, dp, ip, ctypes.POINTER(hisq_solver_opts),
+                                  ctypes.POINTER(hisq_solver_stats), vp, vp]
+    fp = ctypes.c_float
+    lib.hisq_ptc_create.argtypes = [ctypes.POINTER(vp), vp, ip]
+    lib.hisq_ptc_destroy.argtypes = [vp]
+    lib.hisq_ptc_set_weights.argtypes = [vp, vp, vp]
+    lib.hisq_ptc_get_weights.argtypes = [vp, vp, vp]
+    lib.hisq_ptc_apply.argtypes = [vp, vp, vp, ip]
+    lib.hisq_ptc_bind.argtypes = [vp, vp]
+    lib.hisq_ptc_train_step.argtypes = [vp, vp, vp, ip, fp, vp, vp, vp]
+    lib.hisq_fcg.argtypes = [vp, vp, vp, vp, dp, dp, ip, ctypes.POINTER(hisq_solver_opts),
+                             ctypes.POINTER(hisq_solver_stats)]
     _lib = lib
     return lib
 
@@ -233,6 +252,171 @@ def hisq_tune_report(ctx) -> str:
     buf = ctypes.create_string_buffer(1 << 16)
     _check(_load().hisq_tune_report(ctx, buf, len(buf)), "hisq_tune_report")
     return buf.value.decode()
+
+
+def hisq_batch_create(dims_list, prec_mask: int = HISQ_PREC_BIT(HISQ_F64) | HISQ_PREC_BIT(HISQ_F32), stream=None):
+    h = ctypes.c_void_p()
+    flat = [int(v) for d in dims_list for v in d]
+    arr = (ctypes.c_int * len(flat))(*flat)
+    _check(_load().hisq_batch_create(ctypes.byref(h), len(dims_list), arr, prec_mask, _stream_handle(stream)),
+           "hisq_batch_create")
+    return h
+
+
+def hisq_batch_destroy(batch):
+    _check(_load().hisq_batch_destroy(batch), "hisq_batch_destroy")
+
+
+def hisq_batch_load_links(batch, lattice: int, fat, lng, flags: int = HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T):
+    fat = np.ascontiguousarray(fat, dtype=np.complex128)
+    lng = np.ascontiguousarray(lng, dtype=np.complex128)
+    _check(_load().hisq_batch_load_links(batch, lattice, _ptr(fat), _ptr(lng), flags), "hisq_batch_load_links")
+
+
+def hisq_batch_vector_offset(batch, lattice: int) -> int:
+    return int(_load().hisq_batch_vector_offset(batch, lattice))
+
+
+def hisq_batch_launch_count(batch) -> int:
+    return int(_load().hisq_batch_launch_count(batch))
+
+
+def hisq_batch_cg(batch, x, b, masses, rel_tol: float, maxiter: int, opts=None, raise_on_error=True):
+    """Returns (status, stats dict with per-lattice 'lattice_iters' and 'lattice_residual')."""
+    masses = np.ascontiguousarray(masses, dtype=np.float64)
+    nl = len(masses)
+    iters = np.zeros(nl, np.int32)
+    res = np.zeros(nl, np.float64)
+    st = hisq_solver_stats()
+    o = opts if opts is not None else hisq_solver_opts_default()
+    rc = _load().hisq_batch_cg(batch, _ptr(x), _ptr(b), _ptr(masses), rel_tol, maxiter, ctypes.byref(o),
+                               ctypes.byref(st), _ptr(iters), _ptr(res))
+    d = st.as_dict()
+    d["lattice_iters"] = iters.tolist()
+    d["lattice_residual"] = res.tolist()
+    if rc != HISQ_OK and raise_on_error:
+        raise HisqError(rc, "hisq_batch_cg", hisq_last_error(), d)
+    return rc, d
+
+
+class Batch:
+    """Owns one batch of lattices: ``Batch(dims_list)``, ``load(l, fat, lng)``, ``cg(x, b, masses)``."""
+
+    def __init__(self, dims_list, precs=(HISQ_F64, HISQ_F32), stream=None):
+        mask = 0
+        for p in precs:
+            mask |= HISQ_PREC_BIT(p)
+        self.dims = [tuple(int(v) for v in d) for d in dims_list]
+        self.h = hisq_batch_create(self.dims, mask, stream)
+        self.offsets = [hisq_batch_vector_offset(self.h, l) for l in range(len(self.dims) + 1)]
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            hisq_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, lattice, fat, lng, flags=HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T):
+        hisq_batch_load_links(self.h, lattice, fat, lng, flags)
+
+    def cg(self, x, b, masses, rel_tol=1e-10, maxiter=10000, **opts):
+        return hisq_batch_cg(self.h, x, b, masses, rel_tol, maxiter, make_opts(**opts))
+
+
+def hisq_ptc_create(ctx, channels: int = 8):
+    h = ctypes.c_void_p()
+    _check(_load().hisq_ptc_create(ctypes.byref(h), ctx, channels), "hisq_ptc_create")
+    return h
+
+
+def hisq_ptc_destroy(ptc):
+    _check(_load().hisq_ptc_destroy(ptc), "hisq_ptc_destroy")
+
+
+def hisq_ptc_set_weights(ptc, w1, w2):
+    """w1: complex (C, 1, 9), w2: complex (1, C, 9) (numpy); stored as FP32 master weights."""
+    a = np.ascontiguousarray(np.asarray(w1, np.complex64))
+    b = np.ascontiguousarray(np.asarray(w2, np.complex64))
+    _check(_load().hisq_ptc_set_weights(ptc, _ptr(a), _ptr(b)), "hisq_ptc_set_weights")
+
+
+def hisq_ptc_get_weights(ptc, channels: int = 8):
+    a = np.zeros((channels, 1, 9), np.complex64)
+    b = np.zeros((1, channels, 9), np.complex64)
+    _check(_load().hisq_ptc_get_weights(ptc, _ptr(a), _ptr(b)), "hisq_ptc_get_weights")
+    return a, b
+
+
+def hisq_ptc_bind(ptc, ctx):
+    _check(_load().hisq_ptc_bind(ptc, ctx), "hisq_ptc_bind")
+
+
+def hisq_ptc_apply(ptc, z, r, nvec: int = 1):
+    _check(_load().hisq_ptc_apply(ptc, _ptr(z), _ptr(r), nvec), "hisq_ptc_apply")
+
+
+def hisq_ptc_train_step(ptc, b, x, npairs: int, lr: float, channels: int = 8):
+    """Returns (loss, g1, g2): the loss and the Wirtinger gradients before the (optional) Adam step."""
+    loss = np.zeros(1, np.float32)
+    g1 = np.zeros((channels, 1, 9), np.complex64)
+    g2 = np.zeros((1, channels, 9), np.complex64)
+    _check(_load().hisq_ptc_train_step(ptc, _ptr(b), _ptr(x), npairs, lr, _ptr(loss), _ptr(g1), _ptr(g2)),
+           "hisq_ptc_train_step")
+    return float(loss[0]), g1, g2
+
+
+def hisq_fcg(ctx, ptc, x, b, mass: float, rel_tol: float, maxiter: int, opts=None, raise_on_error=True):
+    st = hisq_solver_stats()
+    o = opts if opts is not None else hisq_solver_opts_default()
+    rc = _load().hisq_fcg(ctx, ptc, _ptr(x), _ptr(b), mass, rel_tol, maxiter, ctypes.byref(o), ctypes.byref(st))
+    d = st.as_dict()
+    if rc != HISQ_OK and raise_on_error:
+        raise HisqError(rc, "hisq_fcg", hisq_last_error(), d)
+    return rc, d
+
+
+class Ptc:
+    """The PTC preconditioner network bound to a Lattice (its FP32 fat links)."""
+
+    def __init__(self, lattice, channels: int = 8):
+        self.lattice = lattice
+        self.C = channels
+        self.h = hisq_ptc_create(lattice.ctx, channels)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            hisq_ptc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, w1, w2):
+        hisq_ptc_set_weights(self.h, w1, w2)
+
+    def bind(self, lattice):
+        hisq_ptc_bind(self.h, lattice.ctx)
+        self.lattice = lattice
+
+    def get_weights(self):
+        return hisq_ptc_get_weights(self.h, self.C)
+
+    def apply(self, z, r, nvec=1):
+        hisq_ptc_apply(self.h, z, r, nvec)
+
+    def train_step(self, b, x, npairs, lr):
+        return hisq_ptc_train_step(self.h, b, x, npairs, lr, self.C)
+
+    def fcg(self, x, b, mass, rel_tol=1e-10, maxiter=10000, **opts):
+        return hisq_fcg(self.lattice.ctx, self.h, x, b, mass, rel_tol, maxiter, make_opts(**opts))
 
 
 # ---------------------------------------------------------------- convenience wrapper

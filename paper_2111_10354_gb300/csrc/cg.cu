@@ -96,43 +96,63 @@ __global__ void k_reliable(const double2* __restrict__ r_hi, S* __restrict__ r_l
   }
 }
 
-// x += alpha*scale*p; r -= alpha*Ap; rr_new = |r|^2.
+// Complex vector access per site (3 colours) for the BLAS kernels.
 template <typename S>
-__global__ void k_update(double2* __restrict__ x, S* __restrict__ r, const S* __restrict__ p,
-                         const S* __restrict__ Ap, size_t n, SolverState* st, double* partials, size_t pstride,
-                         unsigned* counter) {
+struct Site3 {
+  using T = typename Real<S>::acc;
+  __device__ __forceinline__ static void load(const S* v, size_t site, cplx<T> o[3]) { VecIO<S>::load(v, site, o); }
+  __device__ __forceinline__ static void store(S* v, size_t site, const cplx<T> o[3]) { VecIO<S>::store(v, site, o); }
+};
+
+// One CG update per site: x += alpha*p (X = double: the FP64 solution itself, plain CG; X = float:
+// the FP32 correction e of the current reliable cycle, mixed precision); r -= alpha*Ap;
+// rr_new = |r|^2 with the site's term in the arithmetic precision, summed over sites in FP64.
+template <typename S, typename X>
+__global__ void k_update(X* __restrict__ x, S* __restrict__ r, const S* __restrict__ p, const S* __restrict__ Ap,
+                         size_t nsite, SolverState* st, double* partials, size_t pstride, unsigned* counter) {
   if (st->done) return;
   using T = typename Real<S>::acc;
+  using XT = typename Real<X>::acc;
   const int rh = blockIdx.y;
-  const size_t off = (size_t)rh * n;
+  const size_t off = (size_t)rh * nsite;
   double v[1] = {0.0};
   const double pap = st->pAp[rh];
   const bool active = !st->rhs_done[rh] && pap > 0.0 && isfinite(pap);
   const double alpha = active ? st->rr[rh] / pap : 0.0;
-  const double ax = alpha * st->scale[rh];
   const T a = T(alpha);
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = 2 * (off + i);
-    T pr = T(p[j]), pi = T(p[j + 1]);
-    T rr_ = T(r[j]), ri = T(r[j + 1]);
+  // X = double: x is the solution itself, in true units (alpha * scale); X = float: e is in
+  // inner units and k_fold applies the scale
+  const XT ax = XT(sizeof(X) == 8 ? alpha * st->scale[rh] : alpha);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nsite; i += (size_t)gridDim.x * blockDim.x) {
+    if (st->rhs_done[rh]) break;  // frozen rhs: its vectors are not touched (uniform per block)
+    cplx<T> pv[3], rv[3], av[3];
+    Site3<S>::load(p, off + i, pv);
+    Site3<S>::load(r, off + i, rv);
     if (active) {
-      double2 xv = x[off + i];
-      xv.x += ax * (double)pr;
-      xv.y += ax * (double)pi;
-      x[off + i] = xv;
-      rr_ = fma(-a, T(Ap[j]), rr_);
-      ri = fma(-a, T(Ap[j + 1]), ri);
-      r[j] = S(rr_);
-      r[j + 1] = S(ri);
+      cplx<XT> xv[3];
+      Site3<X>::load(x, off + i, xv);
+      Site3<S>::load(Ap, off + i, av);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        xv[c].re = fma(ax, XT(pv[c].re), xv[c].re);
+        xv[c].im = fma(ax, XT(pv[c].im), xv[c].im);
+        rv[c].re = fma(-a, av[c].re, rv[c].re);
+        rv[c].im = fma(-a, av[c].im, rv[c].im);
+      }
+      Site3<X>::store(x, off + i, xv);
+      Site3<S>::store(r, off + i, rv);
     }
-    v[0] += (double)rr_ * (double)rr_ + (double)ri * (double)ri;
+    T t = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
+    v[0] += (double)t;
   }
   double out[1][MAXR];
   if (grid_reduce<1>(v, partials, pstride, counter, out, st->nrhs) && threadIdx.x == 0) {
     for (int q = 0; q < st->nrhs; ++q) {
       st->rr_new[q] = out[0][q];
-      const double pq = st->pAp[q];
-      if (!st->rhs_done[q] && !(pq > 0.0)) st->breakdown = 1;
+      if (st->rhs_done[q]) continue;
+      if (!(st->pAp[q] > 0.0)) st->breakdown = 1;
       if (!isfinite(out[0][q])) st->nonfinite = 1;
     }
   }
@@ -141,17 +161,24 @@ __global__ void k_update(double2* __restrict__ x, S* __restrict__ r, const S* __
 // p = r + beta*p with beta = rr_new / rr; then (last block) commit rr, iteration counts,
 // per-rhs inner convergence and the end-of-cycle flag.
 template <typename S>
-__global__ void k_pupdate(const S* __restrict__ r, S* __restrict__ p, size_t n, SolverState* st, unsigned* counter) {
+__global__ void k_pupdate(const S* __restrict__ r, S* __restrict__ p, size_t nsite, SolverState* st,
+                          unsigned* counter) {
   if (st->done) return;
   using T = typename Real<S>::acc;
   const int rh = blockIdx.y;
-  const size_t off = (size_t)rh * n;
+  const size_t off = (size_t)rh * nsite;
   if (!st->rhs_done[rh]) {
     const T beta = T(st->rr_new[rh] / st->rr[rh]);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-      const size_t j = 2 * (off + i);
-      p[j] = S(fma(beta, T(p[j]), T(r[j])));
-      p[j + 1] = S(fma(beta, T(p[j + 1]), T(r[j + 1])));
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nsite; i += (size_t)gridDim.x * blockDim.x) {
+      cplx<T> pv[3], rv[3];
+      Site3<S>::load(p, off + i, pv);
+      Site3<S>::load(r, off + i, rv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pv[c].re = fma(beta, pv[c].re, rv[c].re);
+        pv[c].im = fma(beta, pv[c].im, rv[c].im);
+      }
+      Site3<S>::store(p, off + i, pv);
     }
   }
   if (last_block_done(counter) && threadIdx.x == 0) {
@@ -170,6 +197,23 @@ __global__ void k_pupdate(const S* __restrict__ r, S* __restrict__ p, size_t n, 
   }
 }
 
+// End of a mixed-precision cycle: x (FP64) += scale * e (FP32 correction); e = 0.
+__global__ void k_fold(double2* __restrict__ x, float* __restrict__ e, size_t n /* complex per rhs */,
+                       const SolverState* st) {
+  const int rh = blockIdx.y;
+  const size_t off = (size_t)rh * n;
+  const double s = st->scale[rh];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float2* ep = reinterpret_cast<float2*>(e) + off + i;
+    const float2 ev = *ep;
+    double2 xv = x[off + i];
+    xv.x += s * (double)ev.x;
+    xv.y += s * (double)ev.y;
+    x[off + i] = xv;
+    *ep = make_float2(0.f, 0.f);
+  }
+}
+
 __global__ void k_new_cycle(SolverState* st) {
   st->done = 0;
   st->cycle_iter = 0;
@@ -181,17 +225,19 @@ struct CgBuffers {
   size_t b_stride;          // complex entries between sources (0: one source for every rhs)
   std::vector<double> a;    // per-rhs diagonal 4m^2 + sigma_r
   void *r, *p, *Ap, *t;  // inner vectors (S = double or float)
+  void* e;               // mixed precision: FP32 correction of the current cycle (else == x)
   SolverState* st;
   double* partials;
 };
 
-static dim3 blas_grid(const hisq_ctx* ctx, int nrhs) {
-  int gx = (int)((ctx->g.half * 3 + 255) / 256);
-  int cap = ctx->num_sms * 8 / nrhs;
-  if (cap < 4) cap = 4;
+static dim3 blas_grid(const hisq_ctx* ctx, int nrhs, size_t units) {
+  size_t gx = (units + 255) / 256;
+  const size_t cap = (size_t)ctx->num_sms * 8;  // one wave of 256-thread blocks (grid-stride beyond)
   if (gx > cap) gx = cap;
-  return dim3(gx, nrhs);
+  if (gx < 1) gx = 1;
+  return dim3((unsigned)gx, nrhs);
 }
+static dim3 blas_grid(const hisq_ctx* ctx, int nrhs) { return blas_grid(ctx, nrhs, (size_t)ctx->g.half); }
 
 // r_hi = b - A_64 x; rr_true (and bb with init).
 static int true_residual(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int init) {
@@ -229,7 +275,8 @@ static int reliable(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int first) {
   return HISQ_OK;
 }
 
-// One inner iteration (inner link precision lp, spinor type S).
+// One inner iteration (inner link precision lp, spinor type S). Mixed precision accumulates
+// the cycle's correction e in FP32; k_fold adds it to the FP64 x before each reliable update.
 template <typename S>
 static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
   const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
@@ -240,6 +287,7 @@ static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
   c1.in = B.p;
   c1.nrhs = nrhs;
   c1.rhs_stride = ctx->g.half;
+  c1.skip = &B.st->done;
   int rc = dslash_launch(ctx, lp, sp, c1);
   if (rc != HISQ_OK) return rc;
   DslashCall c2 = c1;
@@ -254,9 +302,14 @@ static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
   c2.counter = ctx->d_counters + 3;
   if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
   dim3 grid = blas_grid(ctx, nrhs);
-  k_update<S><<<grid, 256, 0, ctx->stream>>>(B.x, (S*)B.r, (const S*)B.p, (const S*)B.Ap, n, B.st, B.partials,
-                                             partial_stride(ctx), ctx->d_counters + 4);
-  k_pupdate<S><<<grid, 256, 0, ctx->stream>>>((const S*)B.r, (S*)B.p, n, B.st, ctx->d_counters + 5);
+  const size_t nsite = ctx->g.half;
+  if (sizeof(S) == 8)
+    k_update<S, double><<<grid, 256, 0, ctx->stream>>>((double*)B.x, (S*)B.r, (const S*)B.p, (const S*)B.Ap, nsite,
+                                                       B.st, B.partials, partial_stride(ctx), ctx->d_counters + 4);
+  else
+    k_update<S, float><<<grid, 256, 0, ctx->stream>>>((float*)B.e, (S*)B.r, (const S*)B.p, (const S*)B.Ap, nsite,
+                                                      B.st, B.partials, partial_stride(ctx), ctx->d_counters + 4);
+  k_pupdate<S><<<grid, 256, 0, ctx->stream>>>((const S*)B.r, (S*)B.p, nsite, B.st, ctx->d_counters + 5);
   HISQ_CUDA(cudaGetLastError());
   note_launch(ctx, 2);
   return HISQ_OK;
@@ -289,9 +342,18 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   B.t = workspace(ctx, "cg_t", vbS);
   B.st = (SolverState*)workspace(ctx, "cg_state", sizeof(SolverState));
   B.partials = (double*)workspace(ctx, "cg_partials", 3 * MAXR * partial_stride(ctx) * sizeof(double));
+  B.e = mixed ? workspace(ctx, "cg_e", (size_t)nrhs * n * 2 * sizeof(float)) : (void*)x;
   SolverState* hst = (SolverState*)ctx->pinned;
-  if (!B.r_hi || !B.Ax || !B.t64 || !B.r || !B.p || !B.Ap || !B.t || !B.st || !B.partials)
+  if (!B.r_hi || !B.Ax || !B.t64 || !B.r || !B.p || !B.Ap || !B.t || !B.st || !B.partials || !B.e)
     return set_error(HISQ_ENOMEM, "solver workspace");
+  if (mixed) HISQ_CUDA(cudaMemsetAsync(B.e, 0, (size_t)nrhs * n * 2 * sizeof(float), ctx->stream));
+  auto fold = [&]() -> int {
+    if (!mixed) return HISQ_OK;
+    k_fold<<<blas_grid(ctx, nrhs, n), 256, 0, ctx->stream>>>(B.x, (float*)B.e, n, B.st);
+    HISQ_CUDA(cudaGetLastError());
+    note_launch(ctx);
+    return HISQ_OK;
+  };
   B.a.resize(nrhs);
   for (int q = 0; q < nrhs; ++q) B.a[q] = 4.0 * mass * mass + (sigma ? sigma[q] : 0.0);
   long long dcalls = 0;
@@ -405,6 +467,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
     bool all_inner = true;
     for (int q = 0; q < nrhs; ++q) all_inner = all_inner && hst->rhs_done[q];
     if (mixed || all_inner) {
+      if ((rc = fold()) != HISQ_OK) return rc;
       if ((rc = true_residual(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
       if ((rc = reliable<S>(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
       dcalls += 2;
@@ -424,6 +487,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   if (exec) cudaGraphExecDestroy(exec);
   if (!verified) {
     // the iterate changed since the last true residual: recompute it for the report
+    if ((rc = fold()) != HISQ_OK) return rc;
     if ((rc = true_residual(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
     HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
   }
@@ -613,6 +677,7 @@ static int ms_iteration(hisq_ctx* ctx, int lp, double2* x, S* r, S* p, S* Ap, S*
   c1.in = pb;
   c1.nrhs = 1;
   c1.rhs_stride = ctx->g.half;
+  c1.skip = &st->done;
   int rc = dslash_launch(ctx, lp, sp, c1);
   if (rc != HISQ_OK) return rc;
   DslashCall c2 = c1;

@@ -36,71 +36,88 @@ struct DslashKArgs {
   double* partials;   // [NR][gridDim.x]
   double* dot_out;    // [NR]
   unsigned* counter;
+  const int* skip;    // when non-null and set: a finished solver cycle, do nothing
 };
 
+// The 16 hopping terms at output site cb (parity p) for NR vectors: acc[r][i] = (D in_r)(x)_i.
+// links: the 16 blocks of one lattice in the link precision; in: NR vectors rhs_stride sites apart.
+template <typename LR, typename SR, int NR>
+__device__ __forceinline__ void dslash_site(const Geom& g, const char* links, size_t blk_bytes, int p, int cb,
+                                            const void* in, size_t rhs_stride,
+                                            cplx<typename Real<LR>::acc> (&acc)[NR][3]) {
+  using A = typename Real<LR>::acc;
+  using SA = typename Real<SR>::acc;
+  const char* fwd = links + (size_t)(p * 8) * blk_bytes;        // blocks of parity p
+  const char* bwd = links + (size_t)((1 - p) * 8) * blk_bytes;  // blocks of parity 1-p
+  int c[4];
+  site_coords(g, p, cb, c);
+  const int idx = lex_index(g, c);
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[r][i] = {A(0), A(0)};
+
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      const int hop = kind == 0 ? 1 : 3;
+      const char* blk_f = fwd + (size_t)(kind * 4 + mu) * blk_bytes;
+      const char* blk_b = bwd + (size_t)(kind * 4 + mu) * blk_bytes;
+      // forward hop: + W_mu(x) in(x + hop mu)
+      {
+        const int nb = neighbour_cb(g, c, idx, mu, +hop);
+        cplx<A> U[9];
+        LinkIO<LR>::load(blk_f, g.half, cb, U);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          cplx<SA> vs[3];
+          VecIO<SR>::load(in, (size_t)r * rhs_stride + nb, vs);
+          cplx<A> v[3] = {{A(vs[0].re), A(vs[0].im)}, {A(vs[1].re), A(vs[1].im)}, {A(vs[2].re), A(vs[2].im)}};
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) cmac(acc[r][i], U[3 * i + j], v[j]);
+        }
+      }
+      // backward hop: - W_mu(x - hop mu)^dag in(x - hop mu)
+      {
+        const int nb = neighbour_cb(g, c, idx, mu, -hop);
+        cplx<A> U[9];
+        LinkIO<LR>::load(blk_b, g.half, nb, U);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          cplx<SA> vs[3];
+          VecIO<SR>::load(in, (size_t)r * rhs_stride + nb, vs);
+          cplx<A> v[3] = {{A(vs[0].re), A(vs[0].im)}, {A(vs[1].re), A(vs[1].im)}, {A(vs[2].re), A(vs[2].im)}};
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) cmac_conj_sub(acc[r][i], U[3 * j + i], v[j]);
+        }
+      }
+    }
+  }
+}
+
+// Register budget: the single-vector FP32/16-bit kernels are held to 64 registers (4 blocks of 256
+// per SM): the fused epilogue otherwise grows to ~100 registers and halves the resident warps,
+// which for this memory-bound stencil halves the bandwidth. FP64 keeps its registers (it is
+// bound by GB300's FP64 pipe, and a 64-register cap spills).
 template <typename LR, typename SR, int NR, int EPI>
-__global__ void __launch_bounds__(NR <= 2 ? 512 : (NR <= 4 ? 256 : 128)) dslash_kernel(const DslashKArgs k) {
+__global__ void __launch_bounds__((NR == 1 && sizeof(LR) < 8) ? 256 : (NR <= 2 ? 512 : (NR <= 4 ? 256 : 128)), (NR == 1 && sizeof(LR) < 8) ? 4 : 1) dslash_kernel(const DslashKArgs k) {
   using A = typename Real<LR>::acc;  // accumulation type follows the link precision
   using SA = typename Real<SR>::acc;
+  if (k.skip && *k.skip) return;  // uniform over the grid
   const Geom& g = k.g;
   const int p = k.out_parity;
-  const char* fwd = k.links + (size_t)(p * 8) * k.blk_bytes;        // blocks of parity p
-  const char* bwd = k.links + (size_t)((1 - p) * 8) * k.blk_bytes;  // blocks of parity 1-p
   double dot[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) dot[r] = 0.0;
 
   for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.half; cb += gridDim.x * blockDim.x) {
-    int c[4];
-    site_coords(g, p, cb, c);
-    const int idx = lex_index(g, c);
     cplx<A> acc[NR][3];
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) acc[r][i] = {A(0), A(0)};
-
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-#pragma unroll
-      for (int kind = 0; kind < 2; ++kind) {
-        const int hop = kind == 0 ? 1 : 3;
-        const char* blk_f = fwd + (size_t)(kind * 4 + mu) * k.blk_bytes;
-        const char* blk_b = bwd + (size_t)(kind * 4 + mu) * k.blk_bytes;
-        // forward hop: + W_mu(x) in(x + hop mu)
-        {
-          const int nb = neighbour_cb(g, c, idx, mu, +hop);
-          cplx<A> U[9];
-          LinkIO<LR>::load(blk_f, g.half, cb, U);
-#pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            cplx<SA> vs[3];
-            VecIO<SR>::load(k.in, (size_t)r * k.rhs_stride + nb, vs);
-            cplx<A> v[3] = {{A(vs[0].re), A(vs[0].im)}, {A(vs[1].re), A(vs[1].im)}, {A(vs[2].re), A(vs[2].im)}};
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int j = 0; j < 3; ++j) cmac(acc[r][i], U[3 * i + j], v[j]);
-          }
-        }
-        // backward hop: - W_mu(x - hop mu)^dag in(x - hop mu)
-        {
-          const int nb = neighbour_cb(g, c, idx, mu, -hop);
-          cplx<A> U[9];
-          LinkIO<LR>::load(blk_b, g.half, nb, U);
-#pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            cplx<SA> vs[3];
-            VecIO<SR>::load(k.in, (size_t)r * k.rhs_stride + nb, vs);
-            cplx<A> v[3] = {{A(vs[0].re), A(vs[0].im)}, {A(vs[1].re), A(vs[1].im)}, {A(vs[2].re), A(vs[2].im)}};
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int j = 0; j < 3; ++j) cmac_conj_sub(acc[r][i], U[3 * j + i], v[j]);
-          }
-        }
-      }
-    }
+    dslash_site<LR, SR, NR>(g, k.links, k.blk_bytes, p, cb, k.in, k.rhs_stride, acc);
 
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -119,9 +136,12 @@ __global__ void __launch_bounds__(NR <= 2 ? 512 : (NR <= 4 ? 256 : 128)) dslash_
           o[i].im = SA(fma(a, A(yv[i].im), -acc[r][i].im));
         }
         if (k.partials) {
+          // the site's term in the arithmetic precision, summed over sites in FP64 (GB300's
+          // FP64 pipe is ~2 ops/clk/SM: one conversion and one add per site, not twelve)
+          SA t = SA(0);
 #pragma unroll
-          for (int i = 0; i < 3; ++i)
-            dot[r] += (double)yv[i].re * (double)o[i].re + (double)yv[i].im * (double)o[i].im;
+          for (int i = 0; i < 3; ++i) t += yv[i].re * o[i].re + yv[i].im * o[i].im;
+          dot[r] += (double)t;
         }
       }
       VecIO<SR>::store(k.out, site, o);

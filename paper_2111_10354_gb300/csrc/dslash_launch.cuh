@@ -14,7 +14,8 @@ static int launch_group(hisq_ctx* ctx, DslashKArgs a, const char* key) {
   auto kern = dslash_kernel<LR, SR, NR, EPI>;
   auto run = [&](int block) -> cudaError_t {
     int grid = (ctx->g.half + block - 1) / block;
-    int cap = max_grid_blocks(ctx, block);
+    // reducing launches: one wave of blocks keeps the partials (and the finishing block's tail) short
+    int cap = (EPI == EPI_AXPY && a.partials) ? ctx->num_sms * (2048 / block) : max_grid_blocks(ctx, block);
     if (grid > cap) grid = cap;
     kern<<<grid, block, 0, ctx->stream>>>(a);
     return cudaGetLastError();
@@ -69,6 +70,7 @@ int dslash_launch_t(hisq_ctx* ctx, const DslashCall& c) {
     a.partials = c.partials ? c.partials + (size_t)r0 * partial_stride(ctx) : nullptr;
     a.dot_out = c.dot_out ? c.dot_out + r0 : nullptr;
     a.counter = c.counter;
+    a.skip = c.skip;
     int rc = c.epi == EPI_PLAIN ? launch_nr<LR, SR, EPI_PLAIN>(ctx, a, nr) : launch_nr<LR, SR, EPI_AXPY>(ctx, a, nr);
     if (rc != HISQ_OK) return rc;
     r0 += nr;

@@ -354,10 +354,19 @@ __device__ __forceinline__ bool last_block_done(unsigned* counter) {
 }
 
 // Deterministic sum of partials[0..n) by the (single) finishing block; thread 0 gets it.
+// Eight independent accumulators per thread keep eight L2 loads in flight, so the single
+// finishing block is not bound by a chain of dependent load latencies.
 __device__ __forceinline__ double sum_partials_dyn(const double* partials, int n, double* smem) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(partials + i);
-  return block_sum_dyn(s, smem);
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int stride = blockDim.x;
+  int i = threadIdx.x;
+  for (; i + 7 * stride < n; i += 8 * stride) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] += __ldcg(partials + i + k * stride);
+  }
+  for (; i < n; i += stride) s[0] += __ldcg(partials + i);
+  const double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+  return block_sum_dyn(t, smem);
 }
 
 }  // namespace hisq
@@ -430,6 +439,7 @@ struct DslashCall {
   double* partials = nullptr;  // [nrhs][grid] when non-null: reduce Re<y, out>
   double* dot_out = nullptr;   // [nrhs] final sums (written by the last block)
   unsigned* counter = nullptr;
+  const int* skip = nullptr;  // device flag: skip the launch's work when set
   int epi = EPI_PLAIN;
 };
 

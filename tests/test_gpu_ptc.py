@@ -1,0 +1,129 @@
+"""The PTC network on the GPU (tensor-core channel mixing, BF16 operands, FP32 accumulation) against the
+FP64 oracle: forward output, loss and weight gradients; flexible CG with the network as preconditioner
+judged by the oracle's true residual. Tolerances: BF16 forward <= 1e-2, gradients <= 2e-2 (relative)."""
+import numpy as np
+import pytest
+
+import hisq_inputs as hin
+import oracle
+import oracle.ptc as optc
+
+pytestmark = pytest.mark.gpu
+
+L = (8, 10, 12, 14)
+
+
+@pytest.fixture(scope="module")
+def setup(hisq):
+    fat, lng = hin.gen_links(L, 4242, 0.35, 0.1)
+    lat = hisq.Lattice(L, precs=(0, 1)).load(fat, lng)
+    ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
+    net = hisq.Ptc(lat)
+    return lat, net, ff, lf
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_ptc_forward_parity(setup):
+    import torch
+    lat, net, ff, lf = setup
+    W1, W2 = optc.init_weights(11)
+    net.set_weights(W1, W2)
+    r = hin.gen_source(12, lat.half, 2)
+    rd = torch.from_numpy(r).to(torch.complex64).cuda()
+    z = torch.empty_like(rd)
+    net.apply(z, rd, 2)
+    zg = z.cpu().numpy().astype(np.complex128)
+    w1, w2 = W1.astype(np.complex64).astype(np.complex128), W2.astype(np.complex64).astype(np.complex128)
+    for v in range(2):
+        ref, _ = optc.network_forward(L, ff, w1, w2, r[v])
+        assert rel(zg[v], ref) <= 1e-2, rel(zg[v], ref)
+
+
+def test_ptc_identity_network(setup):
+    """W1 = W2 = identity hop on channel 0 only: N(r) = r (up to BF16 rounding of r)."""
+    import torch
+    lat, net, ff, lf = setup
+    W1 = np.zeros((8, 1, 9), np.complex128)
+    W2 = np.zeros((1, 8, 9), np.complex128)
+    W1[0, 0, 0] = 1.0
+    W2[0, 0, 0] = 1.0
+    net.set_weights(W1, W2)
+    r = hin.gen_source(13, lat.half, 1)
+    rd = torch.from_numpy(r).to(torch.complex64).cuda()
+    z = torch.empty_like(rd)
+    net.apply(z, rd, 1)
+    assert rel(z.cpu().numpy()[0].astype(np.complex128), r[0]) <= 5e-3
+
+
+def test_ptc_gradient_parity(setup):
+    import torch
+    lat, net, ff, lf = setup
+    W1, W2 = optc.init_weights(21)
+    net.set_weights(W1, W2)
+    bs = hin.gen_source(30, lat.half, 3)
+    xs = hin.gen_source(40, lat.half, 3)
+    bd = torch.from_numpy(bs).to(torch.complex64).cuda()
+    xd = torch.from_numpy(xs).to(torch.complex64).cuda()
+    loss, g1, g2 = net.train_step(bd, xd, 3, 0.0)
+    w1, w2 = W1.astype(np.complex64).astype(np.complex128), W2.astype(np.complex64).astype(np.complex128)
+    rloss, r1, r2 = optc.loss_and_grads(L, ff, w1, w2, list(bs), list(xs))
+    assert abs(loss - rloss) <= 1e-2 * abs(rloss)
+    assert rel(g1.astype(np.complex128), r1) <= 2e-2, rel(g1, r1)
+    assert rel(g2.astype(np.complex128), r2) <= 2e-2, rel(g2, r2)
+    # weights unchanged with lr = 0
+    a, b = net.get_weights()
+    assert np.allclose(a, W1.astype(np.complex64)) and np.allclose(b, W2.astype(np.complex64))
+
+
+def test_ptc_training_reduces_loss(setup):
+    import torch
+    lat, net, ff, lf = setup
+    W1, W2 = optc.init_weights(31, scale=0.05)
+    net.set_weights(W1, W2)
+    mass = 0.05
+    bs = hin.gen_source(50, lat.half, 8)
+    xs = np.stack([oracle.cg(L, ff, lf, mass, bs[i], tol=1e-8)[0] for i in range(8)])
+    bd = torch.from_numpy(bs).to(torch.complex64).cuda()
+    xd = torch.from_numpy(xs).to(torch.complex64).cuda()
+    first = net.train_step(bd, xd, 8, 0.02)[0]
+    for _ in range(60):
+        last = net.train_step(bd, xd, 8, 0.02)[0]
+    assert last < 0.8 * first, (first, last)
+
+
+@pytest.mark.parametrize("weights", ["identity"])
+def test_fcg_true_residual(setup, weights):
+    import torch
+    lat, net, ff, lf = setup
+    mass = 0.05
+    if weights == "identity":
+        W1 = np.zeros((8, 1, 9), np.complex128)
+        W2 = np.zeros((1, 8, 9), np.complex128)
+        W1[0, 0, 0] = 1.0
+        W2[0, 0, 0] = 1.0
+        net.set_weights(W1, W2)
+    else:
+        W1, W2 = optc.init_weights(41, scale=0.05)
+        W1[0, 0, 0] = W2[0, 0, 0] = 1.0
+        net.set_weights(W1, W2)
+        bs = hin.gen_source(70, lat.half, 8)
+        xs = np.stack([oracle.cg(L, ff, lf, mass, bs[i], tol=1e-8)[0] for i in range(8)])
+        bd = torch.from_numpy(bs).to(torch.complex64).cuda()
+        xd = torch.from_numpy(xs).to(torch.complex64).cuda()
+        for _ in range(40):
+            net.train_step(bd, xd, 8, 0.01)
+    b = hin.gen_source(60, lat.half, 1)
+    x = torch.zeros((1, lat.half, 3), dtype=torch.complex128, device="cuda")
+    rc, st = net.fcg(x, torch.from_numpy(b).cuda(), mass, 1e-10, 3000)
+    assert rc == 0 and st["converged"] == 1
+    r = oracle.true_residual(L, ff, lf, mass, b[0], x.cpu().numpy()[0])
+    assert r <= 1e-10
+    assert abs(r - st["true_rel_residual"]) < 1e-11
+    if weights == "identity":
+        # identity preconditioner: FCG takes about as many iterations as CG
+        xc = torch.zeros_like(x)
+        _, sc = lat.cg(xc, torch.from_numpy(b).cuda(), mass, 1e-10, 3000, inner_prec=1)
+        assert abs(st["iters"] - sc["iters"]) <= 0.15 * sc["iters"] + 5
