@@ -245,6 +245,31 @@ int hisq_ptc_train_step(hisq_ptc* ptc, const float* b, const float* x, int npair
 int hisq_fcg(hisq_ctx* ctx, hisq_ptc* ptc, double* x, const double* b, double mass, double rel_tol, int maxiter,
              const hisq_solver_opts* opts, hisq_solver_stats* stats);
 
+/* ---------------------------------------------------------------- no-allocation variant */
+/*
+ * Bytes of the fixed device scratch array behind hisq_apply_A_noalloc (32 MiB). Every GPU that
+ * loads the library holds this array until the process exits.
+ */
+#define HISQ_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * hisq_apply_A_noalloc -- the paper has no counterpart; this is a service of the library.
+ * Same result as hisq_apply_A, out = (4 m^2 + sigma) in - D_eo D_oe in, for callers that cannot
+ * allocate device memory when they make the call: code recording into a CUDA graph by stream
+ * capture (a cudaMalloc there breaks the capture), code whose device memory is owned by an
+ * allocator that forbids foreign allocations, and latency-critical loops that cannot take the
+ * device synchronisation of cudaMalloc. hisq_apply_A allocates its odd-site intermediate on first
+ * use; this variant keeps it in a fixed file-scope device array of HISQ_NOALLOC_SCRATCH_BYTES and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ * in, out: device pointers only (host vectors would need staging buffers); nrhs * V/2 * 6 *
+ * sizeof(real of prec) must not exceed HISQ_NOALLOC_SCRATCH_BYTES, else HISQ_EINVAL.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, once per
+ * device, with that device current); make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (several streams or host
+ * threads at once) race on it. Nothing in it needs clearing: each call overwrites what it reads.
+ */
+int hisq_apply_A_noalloc(hisq_ctx* ctx, void* out, const void* in, double mass, double sigma, int prec, int nrhs);
+
 /* ---------------------------------------------------------------- diagnostics */
 const char* hisq_strerror(int code);
 const char* hisq_last_error(void);

@@ -32,6 +32,7 @@ PREC_NAMES = {HISQ_F64: "f64", HISQ_F32: "f32", HISQ_F16: "f16", HISQ_BF16: "bf1
 HISQ_APPLY_PHASES = 1
 HISQ_ANTIPERIODIC_T = 2
 HISQ_PREC_ALL = 0xF
+HISQ_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def HISQ_PREC_BIT(p: int) -> int:
@@ -79,6 +80,7 @@ def _load():
     lib.hisq_load_links_slab.argtypes = [vp, ip, ip, vp, vp, ctypes.c_uint]
     lib.hisq_dslash.argtypes = [vp, ip, vp, vp, ip, ip]
     lib.hisq_apply_A.argtypes = [vp, vp, vp, dp, dp, ip, ip]
+    lib.hisq_apply_A_noalloc.argtypes = [vp, vp, vp, dp, dp, ip, ip]
     lib.hisq_solver_opts_default.argtypes = [ctypes.POINTER(hisq_solver_opts)]
     lib.hisq_solver_opts_default.restype = None
     lib.hisq_cg.argtypes = [vp, vp, vp, ip, dp, dp, ip, ctypes.POINTER(hisq_solver_opts),
@@ -193,6 +195,11 @@ def hisq_dslash(ctx, out_parity: int, out, in_, prec: int, nrhs: int = 1):
 
 def hisq_apply_A(ctx, out, in_, mass: float, sigma: float, prec: int, nrhs: int = 1):
     _check(_load().hisq_apply_A(ctx, _ptr(out), _ptr(in_), mass, sigma, prec, nrhs), "hisq_apply_A")
+
+
+def hisq_apply_A_noalloc(ctx, out, in_, mass: float, sigma: float, prec: int, nrhs: int = 1):
+    """hisq_apply_A without any device allocation (fixed scratch array; device vectors only)."""
+    _check(_load().hisq_apply_A_noalloc(ctx, _ptr(out), _ptr(in_), mass, sigma, prec, nrhs), "hisq_apply_A_noalloc")
 
 
 def hisq_solver_opts_default() -> hisq_solver_opts:

@@ -1,0 +1,72 @@
+"""The no-allocation variant of the A operator against the allocating one, through the C ABI.
+
+hisq_apply_A_noalloc serves callers that cannot allocate device memory during the call (stream
+capture into a CUDA graph, framework-owned allocators, latency-critical loops): it keeps the
+odd-site intermediate in a fixed device array instead of a cudaMalloc'ed workspace. Here its output
+must match hisq_apply_A's within the operator tolerances, on two calls in a row, and sizes beyond
+the fixed maximum must be refused with an error.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import hisq_inputs as hin
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 2e-6, 2: 5e-3, 3: 5e-3}
+
+
+def _device_vec(torch, src, prec):
+    t = torch.from_numpy(np.ascontiguousarray(src))
+    if prec == 0:
+        return t.cuda()
+    if prec == 1:
+        return t.to(torch.complex64).cuda()
+    r = torch.view_as_real(t.to(torch.complex64))
+    return r.to(torch.float16 if prec == 2 else torch.bfloat16).contiguous().cuda()
+
+
+def _to_numpy(torch, t, prec):
+    t = t.cpu()
+    if prec >= 2:
+        t = torch.view_as_complex(t.float().contiguous())
+    return t.to(torch.complex128).numpy()
+
+
+def test_noalloc_matches_apply_A_two_calls(hisq):
+    import torch
+    L = (8, 10, 12, 14)
+    fat, lng = hin.gen_links(L, 1234, 0.3, 0.1)
+    lat = hisq.Lattice(L).load(fat, lng)
+    cases = [(0, 1, 0.05, 0.3, 11), (1, 3, 0.02, 0.0, 12)]  # two calls in a row, different shapes
+    for prec, nrhs, mass, sigma, seed in cases:
+        src = hin.gen_source(seed, lat.half, nrhs)
+        x = _device_vec(torch, src, prec)
+        y_ref, y_na = torch.empty_like(x), torch.empty_like(x)
+        lat.apply_A(y_ref, x, mass, prec, nrhs, sigma=sigma)
+        hisq.hisq_apply_A_noalloc(lat.ctx, y_na, x, mass, sigma, prec, nrhs)
+        torch.cuda.synchronize()
+        a, b = _to_numpy(torch, y_na, prec), _to_numpy(torch, y_ref, prec)
+        err = np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+        assert err <= TOL[prec], (prec, nrhs, err)
+
+
+def test_noalloc_refuses_oversize_and_host_vectors(hisq):
+    import torch
+    L = (16, 16, 16, 16)
+    fat, lng = hin.gen_links(L, 99, 0.3, 0.1)
+    lat = hisq.Lattice(L, precs=(0,)).load(fat, lng)
+    # 16^4 FP64: 1.5 MiB of intermediate per rhs; 32 rhs exceed the fixed maximum
+    nrhs = 32
+    assert nrhs * lat.half * 6 * 8 > hisq.HISQ_NOALLOC_SCRATCH_BYTES
+    x = torch.zeros((nrhs, lat.half, 3), dtype=torch.complex128, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(hisq.HisqError) as e:
+        hisq.hisq_apply_A_noalloc(lat.ctx, y, x, 0.1, 0.0, 0, nrhs)
+    assert e.value.code == hisq.HISQ_EINVAL and "fixed maximum" in str(e.value)
+    xh = np.zeros((1, lat.half, 3), np.complex128)
+    with pytest.raises(hisq.HisqError) as e:
+        hisq.hisq_apply_A_noalloc(lat.ctx, np.zeros_like(xh), xh, 0.1, 0.0, 0, 1)
+    assert e.value.code == hisq.HISQ_EINVAL
