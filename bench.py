@@ -532,10 +532,11 @@ def row_learned(h, torch, hin, epochs=6, batch_pairs=16):
             lat.cg(x[k:k + 16], b[k:k + 16], mass, 1e-10, 20000, nrhs=16, inner_prec=h.HISQ_F32)
         pairs.append((b.to(torch.complex64), x.to(torch.complex64)))
     t_data = time.perf_counter() - t0
-    W1, W2 = optc.init_weights(4000, scale=0.05)
-    W1[0, 0, 0] = W2[0, 0, 0] = 1.0
+    W1, _ = optc.init_weights(4000, scale=0.05)
+    W1[0, 0, 0] = 1.0
     net = h.Ptc(train[0])
-    net.set_weights(W1, W2)
+    net.set_tied(True)  # N = B^dag B: Hermitian positive semi-definite preconditioner
+    net.set_weights(W1, optc.tie(W1))
     t0 = time.perf_counter()
     losses = []
     for ep in range(epochs):

@@ -108,6 +108,18 @@ int hisq_load_links_slab(hisq_ctx* ctx, int t_begin, int t_count, const double* 
                          unsigned flags);
 
 /*
+ * Long-link compression (the paper's "gauge field compression": store part of each link and
+ * recompute the rest from its SU(3)/U(3) structure, Sec. 3). With naik != 0 the context also keeps
+ * the first two rows of every folded long link in its FP32/FP16/BF16 storage, and those Dslash
+ * applications read 12 reals per long link instead of 18 (16% fewer bytes per site), rebuilding
+ * row 2 = conj(row0 x row1) / c with c = naik * eta_mu(x) * (antiperiodic sign), computed from
+ * the site's coordinates. Requires every long link to be naik * SU(3) (as for long links made of
+ * products of SU(3) links); hisq_load_links then returns HISQ_EINVAL otherwise. Call before loading
+ * links (it invalidates loaded links); naik = 0 turns compression off. FP64 is never compressed.
+ */
+int hisq_set_long_compression(hisq_ctx* ctx, double naik);
+
+/*
  * out = D_eo in (out_parity = 0: out on even sites, in on odd sites), or
  * out = D_oe in (out_parity = 1). Vectors in precision prec (its links must be
  * resident), nrhs vectors of V/2 sites back to back; out and in must not overlap.
@@ -223,6 +235,11 @@ int hisq_ptc_destroy(hisq_ptc* ptc);
 /* Host or device FP32 weights in; resets the Adam moments. */
 int hisq_ptc_set_weights(hisq_ptc* ptc, const float* w1, const float* w2);
 int hisq_ptc_get_weights(hisq_ptc* ptc, float* w1, float* w2);
+/* tied = 1: layer 2 becomes the adjoint of layer 1 (W2[0][a][h] = conj(W1[a][0][adj h]), adj
+ * swapping +mu and -mu), so N = B^dag B is Hermitian positive semi-definite -- the form a CG
+ * preconditioner wants. Training then updates w1 only, with the layer-2 gradient carried back;
+ * g1 of hisq_ptc_train_step is the combined gradient. */
+int hisq_ptc_set_tied(hisq_ptc* ptc, int tied);
 /* Rebind the network (weights and Adam moments kept) to another context of the same lattice
  * shape, e.g. to train on several gauge fields. */
 int hisq_ptc_bind(hisq_ptc* ptc, hisq_ctx* ctx);

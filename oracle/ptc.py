@@ -116,3 +116,32 @@ def init_weights(seed, c=8, scale=0.2):
     W1 = (rng.standard_normal((c, 1, NHOP)) + 1j * rng.standard_normal((c, 1, NHOP))) * scale
     W2 = (rng.standard_normal((1, c, NHOP)) + 1j * rng.standard_normal((1, c, NHOP))) * scale
     return W1, W2
+
+
+# ---------------------------------------------------------------- tied (Hermitian) network
+def adjoint_hop(h):
+    """Index of T_h^dag among the hops: 0 -> 0, +mu <-> -mu."""
+    return 0 if h == 0 else (h + 4 if h <= 4 else h - 4)
+
+
+def tie(W1):
+    """Layer-2 weights that make layer 2 the adjoint of layer 1: W2[0][a][h] = conj(W1[a][0][adj(h)]).
+    Then N = B^dag B (B = layer 1 on the embedded even-site input) is Hermitian positive semi-definite."""
+    C = W1.shape[0]
+    W2 = np.zeros((1, C, NHOP), np.complex128)
+    for a in range(C):
+        for h in range(NHOP):
+            W2[0, a, h] = np.conj(W1[a, 0, adjoint_hop(h)])
+    return W2
+
+
+def loss_and_grads_tied(L, fat, W1, bs, xs):
+    """Loss and dLoss/d(conj W1) of the tied network: the layer-1 gradient plus the layer-2
+    gradient carried back through W2 = conj(W1 o adj)."""
+    W2 = tie(W1)
+    loss, g1, g2 = loss_and_grads(L, fat, W1, W2, bs, xs)
+    G = g1.copy()
+    for a in range(W1.shape[0]):
+        for h in range(NHOP):
+            G[a, 0, h] += np.conj(g2[0, a, adjoint_hop(h)])
+    return loss, G

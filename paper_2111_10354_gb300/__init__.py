@@ -95,6 +95,7 @@ def _load():
     lib.hisq_dslash_bytes.argtypes = [vp, ip, ip]
     lib.hisq_dslash_bytes.restype = ctypes.c_double
     lib.hisq_set_autotune.argtypes = [vp, ip]
+    lib.hisq_set_long_compression.argtypes = [vp, dp]
     lib.hisq_launch_count.argtypes = [vp]
     lib.hisq_launch_count.restype = ctypes.c_longlong
     lib.hisq_tune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
@@ -114,6 +115,7 @@ def _load():
     lib.hisq_ptc_get_weights.argtypes = [vp, vp, vp]
     lib.hisq_ptc_apply.argtypes = [vp, vp, vp, ip]
     lib.hisq_ptc_bind.argtypes = [vp, vp]
+    lib.hisq_ptc_set_tied.argtypes = [vp, ip]
     lib.hisq_ptc_train_step.argtypes = [vp, vp, vp, ip, fp, vp, vp, vp]
     lib.hisq_fcg.argtypes = [vp, vp, vp, vp, dp, dp, ip, ctypes.POINTER(hisq_solver_opts),
                              ctypes.POINTER(hisq_solver_stats)]
@@ -247,6 +249,10 @@ def hisq_dslash_bytes(ctx, prec: int, nrhs: int = 1) -> float:
     return float(_load().hisq_dslash_bytes(ctx, prec, nrhs))
 
 
+def hisq_set_long_compression(ctx, naik: float):
+    _check(_load().hisq_set_long_compression(ctx, naik), "hisq_set_long_compression")
+
+
 def hisq_launch_count(ctx) -> int:
     return int(_load().hisq_launch_count(ctx))
 
@@ -359,6 +365,10 @@ def hisq_ptc_get_weights(ptc, channels: int = 8):
     return a, b
 
 
+def hisq_ptc_set_tied(ptc, tied: bool):
+    _check(_load().hisq_ptc_set_tied(ptc, int(tied)), "hisq_ptc_set_tied")
+
+
 def hisq_ptc_bind(ptc, ctx):
     _check(_load().hisq_ptc_bind(ptc, ctx), "hisq_ptc_bind")
 
@@ -409,6 +419,9 @@ class Ptc:
     def set_weights(self, w1, w2):
         hisq_ptc_set_weights(self.h, w1, w2)
 
+    def set_tied(self, tied=True):
+        hisq_ptc_set_tied(self.h, tied)
+
     def bind(self, lattice):
         hisq_ptc_bind(self.h, lattice.ctx)
         self.lattice = lattice
@@ -452,6 +465,11 @@ class Lattice:
 
     def load(self, fat, lng, flags=HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T):
         hisq_load_links(self.ctx, fat, lng, flags)
+        return self
+
+    def compress_long(self, naik=-1.0 / 24.0):
+        """Keep the long links also as two rows (reconstructed in the kernel); reload links after."""
+        hisq_set_long_compression(self.ctx, naik)
         return self
 
     def dslash(self, out_parity, out, in_, prec, nrhs=1):

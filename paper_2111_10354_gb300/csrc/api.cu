@@ -69,7 +69,8 @@ double dslash_bytes(const hisq_ctx* ctx, int lp, int sp, int nrhs) {
 // antiperiodic-t sign (fat at t = Lt-1, long at t >= Lt-3), then store the link in the
 // chunk-plane layout of every resident precision. Non-finite entries raise *bad.
 __global__ void pack_links_kernel(Geom g, const double2* __restrict__ fat, const double2* __restrict__ lng, int t0,
-                                  int nt, unsigned flags, char* l64, char* l32, char* l16, char* lbf, int* bad) {
+                                  int nt, unsigned flags, char* l64, char* l32, char* l16, char* lbf, int* bad,
+                                  double naik, char* c32, char* c16, char* cbf) {
   const int slab = g.L[0] * g.L[1] * g.L[2];
   const int n = slab * nt;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -102,6 +103,40 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ fat, const
           U[k] = {sign * v.x, sign * v.y};
         }
         if (!finite) atomicOr(bad, 1);
+        if (kind == 1 && naik != 0.0 && finite) {
+          // compressed copy: the link must be c * V with V in SU(3), c = naik * (its fold sign)
+          const double ic = 1.0 / (naik * sign);
+          double err = 0.0;
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+              double re = 0.0, im = 0.0;
+              for (int k = 0; k < 3; ++k) {  // (V V^dag)_ij
+                const cplx<double> a = U[3 * i + k], b = U[3 * j + k];
+                re += a.re * b.re + a.im * b.im;
+                im += a.im * b.re - a.re * b.im;
+              }
+              re = re * ic * ic - (i == j ? 1.0 : 0.0);
+              im = im * ic * ic;
+              err = fmax(err, fmax(fabs(re), fabs(im)));
+            }
+          // det V via row0 . (row1 x row2)
+          const cplx<double>* u = U;
+          auto mul = [](cplx<double> a, cplx<double> b) { return cplx<double>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; };
+          cplx<double> c0 = mul(u[4], u[8]), c1 = mul(u[5], u[7]);
+          cplx<double> d0 = {c0.re - c1.re, c0.im - c1.im};
+          cplx<double> c2 = mul(u[5], u[6]), c3 = mul(u[3], u[8]);
+          cplx<double> d1 = {c2.re - c3.re, c2.im - c3.im};
+          cplx<double> c4 = mul(u[3], u[7]), c5 = mul(u[4], u[6]);
+          cplx<double> d2 = {c4.re - c5.re, c4.im - c5.im};
+          cplx<double> e0 = mul(u[0], d0), e1 = mul(u[1], d1), e2 = mul(u[2], d2);
+          const double dre = (e0.re + e1.re + e2.re) * ic * ic * ic - 1.0, dim = (e0.im + e1.im + e2.im) * ic * ic * ic;
+          err = fmax(err, fmax(fabs(dre), fabs(dim)));
+          if (!(err <= 1e-9)) atomicOr(bad, 2);
+          const size_t cblk = (size_t)(par * 4 + mu);
+          if (c32) Link12IO<float>::store(c32 + cblk * long12_block_bytes(HISQ_F32, g.half), g.half, cb, U);
+          if (c16) Link12IO<__half>::store(c16 + cblk * long12_block_bytes(HISQ_F16, g.half), g.half, cb, U);
+          if (cbf) Link12IO<__nv_bfloat16>::store(cbf + cblk * long12_block_bytes(HISQ_BF16, g.half), g.half, cb, U);
+        }
         const size_t blk = (size_t)((par * 2 + kind) * 4 + mu);
         if (l64) LinkIO<double>::store(l64 + blk * link_block_bytes(HISQ_F64, g.half), g.half, cb, U);
         if (l32) LinkIO<float>::store(l32 + blk * link_block_bytes(HISQ_F32, g.half), g.half, cb, U);
@@ -119,7 +154,8 @@ int pack_links_slab(hisq_ctx* ctx, const double* d_fat, const double* d_long, in
   if (grid > ctx->num_sms * 32) grid = ctx->num_sms * 32;
   pack_links_kernel<<<grid, block, 0, ctx->stream>>>(ctx->g, (const double2*)d_fat, (const double2*)d_long, t0, nt,
                                                      flags, ctx->links[0], ctx->links[1], ctx->links[2],
-                                                     ctx->links[3], ctx->d_flag);
+                                                     ctx->links[3], ctx->d_flag, ctx->naik, ctx->long12[1],
+                                                     ctx->long12[2], ctx->long12[3]);
   HISQ_CUDA(cudaGetLastError());
   note_launch(ctx);
   return HISQ_OK;
@@ -225,7 +261,10 @@ int hisq_create(hisq_ctx** out, const int dims[4], unsigned prec_mask, void* str
 int hisq_destroy(hisq_ctx* c) {
   if (!c) return HISQ_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (int p = 0; p < 4; ++p) cudaFree(c->links[p]);
+  for (int p = 0; p < 4; ++p) {
+    cudaFree(c->links[p]);
+    cudaFree(c->long12[p]);
+  }
   for (auto& kv : c->ws) cudaFree(kv.second.ptr);
   cudaFree(c->d_counters);
   cudaFree(c->d_flag);
@@ -268,7 +307,10 @@ int hisq_load_links_slab(hisq_ctx* c, int t_begin, int t_count, const double* fa
   HISQ_CUDA(cudaStreamSynchronize(c->stream));
   if (bad) {
     for (auto& v : c->t_loaded) v = 0;
-    return set_error(HISQ_ENONFINITE, "non-finite link entries in t-slab [%d, %d)", t_begin, t_begin + t_count);
+    if (bad & 1)
+      return set_error(HISQ_ENONFINITE, "non-finite link entries in t-slab [%d, %d)", t_begin, t_begin + t_count);
+    return set_error(HISQ_EINVAL, "long links in t-slab [%d, %d) are not naik * SU(3): they cannot be compressed",
+                     t_begin, t_begin + t_count);
   }
   for (int t = t_begin; t < t_begin + t_count; ++t) c->t_loaded[t] = 1;
   bool all = true;
@@ -377,6 +419,29 @@ int hisq_apply_A(hisq_ctx* c, void* out, const void* in, double mass, double sig
 }
 
 long long hisq_launch_count(const hisq_ctx* c) { return c ? c->launches : 0; }
+
+int hisq_set_long_compression(hisq_ctx* c, double naik) {
+  if (!c) return set_error(HISQ_EINVAL, "null context");
+  if (!(naik == naik) || fabs(naik) > 1e6) return set_error(HISQ_EINVAL, "bad Naik coefficient");
+  if (naik == c->naik) return HISQ_OK;
+  cudaStreamSynchronize(c->stream);
+  for (int p = 1; p < 4; ++p) {
+    cudaFree(c->long12[p]);
+    c->long12[p] = nullptr;
+    if (naik != 0.0 && c->links[p]) {
+      cudaError_t e = cudaMalloc((void**)&c->long12[p], 8 * long12_block_bytes(p, c->g.half));
+      if (e != cudaSuccess) {
+        c->naik = 0.0;
+        return cuda_error(e, "compressed long-link storage");
+      }
+    }
+  }
+  c->naik = naik;
+  // the compressed copy is written when links are loaded: links must be (re)loaded now
+  for (auto& v : c->t_loaded) v = 0;
+  c->links_ready = false;
+  return HISQ_OK;
+}
 
 double hisq_dslash_bytes(const hisq_ctx* c, int prec, int nrhs) {
   if (!c || prec < 0 || prec > 3) return 0.0;

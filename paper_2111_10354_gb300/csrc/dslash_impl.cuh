@@ -37,14 +37,26 @@ struct DslashKArgs {
   double* dot_out;    // [NR]
   unsigned* counter;
   const int* skip;    // when non-null and set: a finished solver cycle, do nothing
+  const char* long12;  // compressed long links (COMP variants)
+  size_t blk12;
+  float inv_naik;
+  unsigned flags;      // load flags: phases / antiperiodic t (fold signs of compressed links)
+};
+
+// What the compressed-long-link path needs at one site.
+struct Comp12 {
+  const char* long12;
+  size_t blk12;
+  float inv_naik;
+  unsigned flags;
 };
 
 // The 16 hopping terms at output site cb (parity p) for NR vectors: acc[r][i] = (D in_r)(x)_i.
 // links: the 16 blocks of one lattice in the link precision; in: NR vectors rhs_stride sites apart.
-template <typename LR, typename SR, int NR>
+template <typename LR, typename SR, int NR, bool COMP = false>
 __device__ __forceinline__ void dslash_site(const Geom& g, const char* links, size_t blk_bytes, int p, int cb,
                                             const void* in, size_t rhs_stride,
-                                            cplx<typename Real<LR>::acc> (&acc)[NR][3]) {
+                                            cplx<typename Real<LR>::acc> (&acc)[NR][3], const Comp12& cz = Comp12{}) {
   using A = typename Real<LR>::acc;
   using SA = typename Real<SR>::acc;
   const char* fwd = links + (size_t)(p * 8) * blk_bytes;        // blocks of parity p
@@ -68,7 +80,17 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const char* links, si
       {
         const int nb = neighbour_cb(g, c, idx, mu, +hop);
         cplx<A> U[9];
-        LinkIO<LR>::load(blk_f, g.half, cb, U);
+        if constexpr (COMP && sizeof(LR) < 8) {
+          if (kind == 1) {
+            Link12IO<LR>::load(cz.long12 + (size_t)(p * 4 + mu) * cz.blk12, g.half, cb, U);
+            const int sg = folded_long_sign(g, cz.flags, mu, c[0], c[1], c[2], c[3]);
+            reconstruct_row2(U, A(sg) * A(cz.inv_naik));
+          } else {
+            LinkIO<LR>::load(blk_f, g.half, cb, U);
+          }
+        } else {
+          LinkIO<LR>::load(blk_f, g.half, cb, U);
+        }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           cplx<SA> vs[3];
@@ -84,7 +106,19 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const char* links, si
       {
         const int nb = neighbour_cb(g, c, idx, mu, -hop);
         cplx<A> U[9];
-        LinkIO<LR>::load(blk_b, g.half, nb, U);
+        if constexpr (COMP && sizeof(LR) < 8) {
+          if (kind == 1) {
+            Link12IO<LR>::load(cz.long12 + (size_t)((1 - p) * 4 + mu) * cz.blk12, g.half, nb, U);
+            // the link sits at y = x - 3mu: only its t coordinate can change the fold sign
+            const int yt = mu == 3 ? (c[3] >= 3 ? c[3] - 3 : c[3] - 3 + g.L[3]) : c[3];
+            const int sg = folded_long_sign(g, cz.flags, mu, c[0], c[1], c[2], yt);
+            reconstruct_row2(U, A(sg) * A(cz.inv_naik));
+          } else {
+            LinkIO<LR>::load(blk_b, g.half, nb, U);
+          }
+        } else {
+          LinkIO<LR>::load(blk_b, g.half, nb, U);
+        }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           cplx<SA> vs[3];
@@ -104,8 +138,16 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const char* links, si
 // per SM): the fused epilogue otherwise grows to ~100 registers and halves the resident warps,
 // which for this memory-bound stencil halves the bandwidth. FP64 keeps its registers (it is
 // bound by GB300's FP64 pipe, and a 64-register cap spills).
-template <typename LR, typename SR, int NR, int EPI>
-__global__ void __launch_bounds__((NR == 1 && sizeof(LR) < 8) ? 256 : (NR <= 2 ? 512 : (NR <= 4 ? 256 : 128)), (NR == 1 && sizeof(LR) < 8) ? 4 : 1) dslash_kernel(const DslashKArgs k) {
+template <typename LR, int NR>
+struct DslashBounds {
+  static constexpr int threads = NR == 1 ? (sizeof(LR) < 8 ? 256 : 512) : (NR == 2 ? 512 : (NR == 4 ? 256 : 128));
+  // FP32/16-bit: 64 registers for one vector, 128 for groups of 4 and 8 (enough warps in flight)
+  static constexpr int min_blocks = sizeof(LR) == 8 ? 1 : (NR == 1 ? 4 : (NR == 2 ? 1 : (NR == 4 ? 2 : (NR == 8 ? 4 : 1))));
+};
+
+template <typename LR, typename SR, int NR, int EPI, bool COMP = false>
+__global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR, NR>::min_blocks)
+    dslash_kernel(const DslashKArgs k) {
   using A = typename Real<LR>::acc;  // accumulation type follows the link precision
   using SA = typename Real<SR>::acc;
   if (k.skip && *k.skip) return;  // uniform over the grid
@@ -117,7 +159,8 @@ __global__ void __launch_bounds__((NR == 1 && sizeof(LR) < 8) ? 256 : (NR <= 2 ?
 
   for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.half; cb += gridDim.x * blockDim.x) {
     cplx<A> acc[NR][3];
-    dslash_site<LR, SR, NR>(g, k.links, k.blk_bytes, p, cb, k.in, k.rhs_stride, acc);
+    dslash_site<LR, SR, NR, COMP>(g, k.links, k.blk_bytes, p, cb, k.in, k.rhs_stride, acc,
+                                  Comp12{k.long12, k.blk12, k.inv_naik, k.flags});
 
 #pragma unroll
     for (int r = 0; r < NR; ++r) {

@@ -9,9 +9,9 @@
 
 namespace hisq {
 
-template <typename LR, typename SR, int NR, int EPI>
+template <typename LR, typename SR, int NR, int EPI, bool COMP>
 static int launch_group(hisq_ctx* ctx, DslashKArgs a, const char* key) {
-  auto kern = dslash_kernel<LR, SR, NR, EPI>;
+  auto kern = dslash_kernel<LR, SR, NR, EPI, COMP>;
   auto run = [&](int block) -> cudaError_t {
     int grid = (ctx->g.half + block - 1) / block;
     // reducing launches: one wave of blocks keeps the partials (and the finishing block's tail) short
@@ -28,24 +28,25 @@ static int launch_group(hisq_ctx* ctx, DslashKArgs a, const char* key) {
   return HISQ_OK;
 }
 
-template <typename LR, typename SR, int EPI>
+template <typename LR, typename SR, int EPI, bool COMP>
 static int launch_nr(hisq_ctx* ctx, const DslashKArgs& a, int nr) {
   char key[64];
-  snprintf(key, sizeof key, "dslash/l%d/s%d/nr%d/e%d", Real<LR>::prec, Real<SR>::prec, nr, EPI);
+  snprintf(key, sizeof key, "dslash/l%d/s%d/nr%d/e%d/c%d", Real<LR>::prec, Real<SR>::prec, nr, EPI, (int)COMP);
   switch (nr) {
-    case 1: return launch_group<LR, SR, 1, EPI>(ctx, a, key);
-    case 2: return launch_group<LR, SR, 2, EPI>(ctx, a, key);
-    case 4: return launch_group<LR, SR, 4, EPI>(ctx, a, key);
-    case 8: return launch_group<LR, SR, (sizeof(LR) == 8 ? 4 : 8), EPI>(ctx, a, key);
-    case 16: return launch_group<LR, SR, (sizeof(LR) == 8 ? 4 : 16), EPI>(ctx, a, key);
+    case 1: return launch_group<LR, SR, 1, EPI, COMP>(ctx, a, key);
+    case 2: return launch_group<LR, SR, 2, EPI, COMP>(ctx, a, key);
+    case 4: return launch_group<LR, SR, 4, EPI, COMP>(ctx, a, key);
+    case 8: return launch_group<LR, SR, (sizeof(LR) == 8 ? 4 : 8), EPI, COMP>(ctx, a, key);
+    case 16: return launch_group<LR, SR, (sizeof(LR) == 8 ? 4 : 16), EPI, COMP>(ctx, a, key);
   }
   return set_error(HISQ_EINVAL, "unsupported rhs group %d", nr);
 }
 
-// Largest rhs group per launch: FP64 accumulators cap it at 4 (register budget).
+// Largest rhs group per launch (register budget): FP64 4, others 8 -- a group of 16 needs more
+// than the 255 registers a thread can hold and spills (measured 5x slower than two groups of 8).
 template <typename LR>
 static int max_group() {
-  return sizeof(LR) == 8 ? 4 : 16;
+  return sizeof(LR) == 8 ? 4 : 8;
 }
 
 template <typename LR, typename SR>
@@ -71,7 +72,24 @@ int dslash_launch_t(hisq_ctx* ctx, const DslashCall& c) {
     a.dot_out = c.dot_out ? c.dot_out + r0 : nullptr;
     a.counter = c.counter;
     a.skip = c.skip;
-    int rc = c.epi == EPI_PLAIN ? launch_nr<LR, SR, EPI_PLAIN>(ctx, a, nr) : launch_nr<LR, SR, EPI_AXPY>(ctx, a, nr);
+    // compressed long links (two rows, third reconstructed) whenever the context keeps them
+    const bool comp = sizeof(LR) < 8 && ctx->naik != 0.0 && ctx->long12[Real<LR>::prec] != nullptr;
+    a.long12 = comp ? ctx->long12[Real<LR>::prec] : nullptr;
+    a.blk12 = long12_block_bytes(Real<LR>::prec, ctx->g.half);
+    a.inv_naik = comp ? (float)(1.0 / ctx->naik) : 0.f;
+    a.flags = ctx->load_flags;
+    int rc;
+    if constexpr (sizeof(LR) < 8) {
+      if (comp)
+        rc = c.epi == EPI_PLAIN ? launch_nr<LR, SR, EPI_PLAIN, true>(ctx, a, nr)
+                                : launch_nr<LR, SR, EPI_AXPY, true>(ctx, a, nr);
+      else
+        rc = c.epi == EPI_PLAIN ? launch_nr<LR, SR, EPI_PLAIN, false>(ctx, a, nr)
+                                : launch_nr<LR, SR, EPI_AXPY, false>(ctx, a, nr);
+    } else {
+      rc = c.epi == EPI_PLAIN ? launch_nr<LR, SR, EPI_PLAIN, false>(ctx, a, nr)
+                              : launch_nr<LR, SR, EPI_AXPY, false>(ctx, a, nr);
+    }
     if (rc != HISQ_OK) return rc;
     r0 += nr;
   }

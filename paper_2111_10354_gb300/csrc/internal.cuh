@@ -248,6 +248,98 @@ struct LinkIO<__half> : LinkIO16<__half> {};
 template <>
 struct LinkIO<__nv_bfloat16> : LinkIO16<__nv_bfloat16> {};
 
+// ------------------------------------------------------------------ compressed long links
+// A folded long link is c * V with V in SU(3) and c = naik * eta_mu(x) * (boundary sign), so its
+// first two rows (12 reals) determine it: row2 = conj(row0 x row1) / c. Storage per block
+// (parity, mu) of the low precisions: FP32 3 planes of float4 (entries 0-1, 2-3, 4-5);
+// FP16/BF16 one 16-byte plane (entries 0-3) and one 8-byte plane (entries 4-5).
+__host__ __device__ inline size_t long12_block_bytes(int prec, int half) { return (size_t)half * 12 * real_size(prec); }
+
+template <typename T>
+__device__ __forceinline__ void reconstruct_row2(cplx<T> U[9], T inv_c) {
+  auto cross = [](const cplx<T>& a, const cplx<T>& b, const cplx<T>& c, const cplx<T>& d) {
+    // conj(a*b - c*d)
+    cplx<T> r;
+    r.re = (a.re * b.re - a.im * b.im) - (c.re * d.re - c.im * d.im);
+    r.im = -((a.re * b.im + a.im * b.re) - (c.re * d.im + c.im * d.re));
+    return r;
+  };
+  cplx<T> r6 = cross(U[1], U[5], U[2], U[4]);
+  cplx<T> r7 = cross(U[2], U[3], U[0], U[5]);
+  cplx<T> r8 = cross(U[0], U[4], U[1], U[3]);
+  U[6] = {r6.re * inv_c, r6.im * inv_c};
+  U[7] = {r7.re * inv_c, r7.im * inv_c};
+  U[8] = {r8.re * inv_c, r8.im * inv_c};
+}
+
+template <typename R>
+struct Link12IO;
+template <>
+struct Link12IO<float> {
+  __device__ __forceinline__ static void load(const char* blk, int half, int cb, cplx<float> U[9]) {
+    const float4* p = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float4 v = ld_stream(p + (size_t)j * half + cb);
+      U[2 * j] = {v.x, v.y};
+      U[2 * j + 1] = {v.z, v.w};
+    }
+  }
+  __device__ __forceinline__ static void store(char* blk, int half, int cb, const cplx<double> U[9]) {
+    float4* p = reinterpret_cast<float4*>(blk);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      p[(size_t)j * half + cb] = make_float4((float)U[2 * j].re, (float)U[2 * j].im, (float)U[2 * j + 1].re,
+                                             (float)U[2 * j + 1].im);
+  }
+};
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+template <typename H>
+struct Link12IO16 {
+  __device__ __forceinline__ static void load(const char* blk, int half, int cb, cplx<float> U[9]) {
+    uint4 v = ld_stream(reinterpret_cast<const uint4*>(blk) + cb);
+    U[0] = unpack2<H>(v.x);
+    U[1] = unpack2<H>(v.y);
+    U[2] = unpack2<H>(v.z);
+    U[3] = unpack2<H>(v.w);
+    uint2 w = ld_stream(reinterpret_cast<const uint2*>(blk + (size_t)16 * half) + cb);
+    U[4] = unpack2<H>(w.x);
+    U[5] = unpack2<H>(w.y);
+  }
+  __device__ __forceinline__ static void store(char* blk, int half, int cb, const cplx<double> U[9]) {
+    uint4 v;
+    v.x = LinkIO16<H>::pack(U[0].re, U[0].im);
+    v.y = LinkIO16<H>::pack(U[1].re, U[1].im);
+    v.z = LinkIO16<H>::pack(U[2].re, U[2].im);
+    v.w = LinkIO16<H>::pack(U[3].re, U[3].im);
+    reinterpret_cast<uint4*>(blk)[cb] = v;
+    uint2 w;
+    w.x = LinkIO16<H>::pack(U[4].re, U[4].im);
+    w.y = LinkIO16<H>::pack(U[5].re, U[5].im);
+    reinterpret_cast<uint2*>(blk + (size_t)16 * half)[cb] = w;
+  }
+};
+template <>
+struct Link12IO<__half> : Link12IO16<__half> {};
+template <>
+struct Link12IO<__nv_bfloat16> : Link12IO16<__nv_bfloat16> {};
+
+// Sign of a folded link from its site's coordinates: eta_mu(x) and, for a long link in t, the
+// antiperiodic sign at t >= Lt-3.
+__device__ __forceinline__ int folded_long_sign(const Geom& g, unsigned flags, int mu, int x0, int x1, int x2, int t) {
+  int s = 1;
+  if (flags & HISQ_APPLY_PHASES) {
+    const int sum = (mu > 0 ? x0 : 0) + (mu > 1 ? x1 : 0) + (mu > 2 ? x2 : 0);
+    if (sum & 1) s = -s;
+  }
+  if ((flags & HISQ_ANTIPERIODIC_T) && mu == 3 && t >= g.L[3] - 3) s = -s;
+  return s;
+}
+
 // ------------------------------------------------------------------ vector access ([cb][3] complex<R>)
 template <typename R>
 struct VecIO;
@@ -394,6 +486,8 @@ struct hisq_ctx {
   unsigned* d_counters = nullptr;    // last-block counters (zeroed), 64 entries
   int* d_flag = nullptr;             // device error flag
   long long launches = 0;            // kernels executed (eager + graph nodes)
+  double naik = 0.0;                 // != 0: long links also stored compressed (two rows), see below
+  char* long12[4] = {nullptr, nullptr, nullptr, nullptr};  // per low precision, 8 blocks (parity, mu)
   bool capturing = false;            // inside this library's own stream capture
 };
 

@@ -84,6 +84,59 @@ __device__ __forceinline__ void transport(const PtcGeom& G, const float2* __rest
   }
 }
 
+// T_h psi_b at site idx for CIN channels at once: the link is loaded once per hop and the CIN
+// neighbour vectors are loaded together (memory-level parallelism).
+template <int CIN>
+__device__ __forceinline__ void transport_multi(const PtcGeom& G, const float2* __restrict__ psi, const int c[4],
+                                                int idx, int h, cplx<float> (&out)[CIN][3]) {
+  const Geom& g = G.g;
+  const size_t cstride = (size_t)g.V * 3;
+  if (h == 0) {
+#pragma unroll
+    for (int b = 0; b < CIN; ++b)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 v = psi[b * cstride + (size_t)idx * 3 + k];
+        out[b][k] = {v.x, v.y};
+      }
+    return;
+  }
+  const int mu = (h - 1) & 3;
+  const bool fwd = h <= 4;
+  const int cm = c[mu] + (fwd ? 1 : -1);
+  int n = idx + (fwd ? g.stride[mu] : -g.stride[mu]);
+  if (cm >= g.L[mu]) n -= g.L[mu] * g.stride[mu];
+  if (cm < 0) n += g.L[mu] * g.stride[mu];
+  const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const int lpar = fwd ? par : 1 - par;
+  const int lcb = fwd ? (idx >> 1) : (n >> 1);
+  cplx<float> U[9];
+  LinkIO<float>::load(G.fat32 + (size_t)(lpar * 8 + mu) * G.blk_bytes, g.half, lcb, U);
+  float2 v[CIN][3];
+#pragma unroll
+  for (int b = 0; b < CIN; ++b)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[b][k] = psi[b * cstride + (size_t)n * 3 + k];
+#pragma unroll
+  for (int b = 0; b < CIN; ++b)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cplx<float> a = {0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const cplx<float> w = {v[b][j].x, v[b][j].y};
+        if (fwd) cmac(a, U[3 * i + j], w);
+        else cmac_conj(a, U[3 * j + i], w);
+      }
+      out[b][i] = a;
+    }
+}
+
+// A pair (re, im) of bf16 at columns (col, col+1), col even: one 4-byte store.
+__device__ __forceinline__ void put_bf16x2(unsigned char* tile, int row, int col, int K2, float re, float im) {
+  *reinterpret_cast<__nv_bfloat162*>(tile + tc::kmajor_offset(row, col, K2)) = __floats2bfloat162_rn(re, im);
+}
+
 // Site of output row `row` of tile `tile`: full lattice (lexicographic) or even sites (cb order).
 __device__ __forceinline__ bool tile_site(const Geom& g, bool even_only, int tile, int row, int c[4], int* idx,
                                           int* out_index) {
@@ -113,7 +166,7 @@ __device__ __forceinline__ void put_bf16(unsigned char* tile, int row, int col, 
 // out: [COUT][n_out][3] float2 with n_out = V (full) or V/2 (even sites, cb order).
 // W: [COUT][CIN][9] float2 (FP32 master weights, rounded to BF16 for the tensor cores).
 template <int CIN, int COUT, bool OUT_EVEN>
-__global__ void __launch_bounds__(128) k_ptc_forward(const PtcGeom G, const float2* __restrict__ in,
+__global__ void __launch_bounds__(256) k_ptc_forward(const PtcGeom G, const float2* __restrict__ in,
                                                      float2* __restrict__ out, const float2* __restrict__ W,
                                                      int* err, const int* skip) {
   if (skip && *skip) return;  // a solver cycle that has already finished (uniform)
@@ -153,21 +206,25 @@ __global__ void __launch_bounds__(128) k_ptc_forward(const PtcGeom G, const floa
   bool failed = false;
 
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    int c[4], idx, oi;
-    const bool valid = tile_site(g, OUT_EVEN, tile, tid, c, &idx, &oi);
-#pragma unroll 1
-    for (int b = 0; b < CIN; ++b) {
-#pragma unroll 1
-      for (int h = 0; h < NHOP; ++h) {
-        cplx<float> u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (valid) transport(G, in + (size_t)b * g.V * 3, c, idx, h, u);
+    // fill: work item = (row, hop); consecutive threads take consecutive sites
+    for (int item = tid; item < PTC_TILE * NHOP; item += blockDim.x) {
+      const int row = item % PTC_TILE, h = item / PTC_TILE;
+      int c[4], idx, oi;
+      cplx<float> u[CIN][3];
+      if (tile_site(g, OUT_EVEN, tile, row, c, &idx, &oi)) {
+        transport_multi<CIN>(G, in, c, idx, h, u);
+      } else {
+#pragma unroll
+        for (int b = 0; b < CIN; ++b)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) u[b][k] = {0.f, 0.f};
+      }
+#pragma unroll
+      for (int b = 0; b < CIN; ++b) {
         const int k = b * NHOP + h;
 #pragma unroll
-        for (int col = 0; col < 3; ++col) {
-          unsigned char* Ac = A + col * PTC_TILE * K2 * 2;
-          put_bf16(Ac, tid, 2 * k, K2, u[col].re);
-          put_bf16(Ac, tid, 2 * k + 1, K2, u[col].im);
-        }
+        for (int col = 0; col < 3; ++col)
+          put_bf16x2(A + col * PTC_TILE * K2 * 2, row, 2 * k, K2, u[b][col].re, u[b][col].im);
       }
     }
     tc::fence_smem_to_async();
@@ -191,13 +248,19 @@ __global__ void __launch_bounds__(128) k_ptc_forward(const PtcGeom G, const floa
       break;
     }
     tc::fence_after_sync();
+    // readout: warp w reads TMEM lanes 32*(w%4).. (rows) for colours w/4, w/4 + 2, ...
+    {
+      const int q = warp & 3, row = 32 * q + (tid & 31);
+      int c[4], idx, oi;
+      const bool valid = tile_site(g, OUT_EVEN, tile, row, c, &idx, &oi);
 #pragma unroll 1
-    for (int col = 0; col < 3; ++col) {
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + col * N2, v);
-      if (valid) {
+      for (int col = warp >> 2; col < 3; col += (int)(blockDim.x >> 7)) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + col * N2, v);
+        if (valid) {
 #pragma unroll
-        for (int a = 0; a < COUT; ++a) out[((size_t)a * n_out + oi) * 3 + col] = make_float2(v[2 * a], v[2 * a + 1]);
+          for (int a = 0; a < COUT; ++a) out[((size_t)a * n_out + oi) * 3 + col] = make_float2(v[2 * a], v[2 * a + 1]);
+        }
       }
     }
     tc::fence_before_sync();
@@ -489,6 +552,27 @@ __global__ void k_embed_even(const Geom g, const float2* __restrict__ r, float2*
   }
 }
 
+__device__ __forceinline__ int adj_hop(int h) { return h == 0 ? 0 : (h <= 4 ? h + 4 : h - 4); }
+
+// Tied network: W2[0][a][h] = conj(W1[a][0][adj(h)]).
+__global__ void k_tie(const float2* __restrict__ w1, float2* __restrict__ w2, int C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C * NHOP) return;
+  const int a = i / NHOP, h = i % NHOP;
+  const float2 w = w1[a * NHOP + adj_hop(h)];
+  w2[i] = make_float2(w.x, -w.y);
+}
+
+// Tied gradient: G1[a][0][h] += conj(G2[0][a][adj(h)]).
+__global__ void k_tie_grad(float2* __restrict__ g1, const float2* __restrict__ g2, int C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C * NHOP) return;
+  const int a = i / NHOP, h = i % NHOP;
+  const float2 g = g2[a * NHOP + adj_hop(h)];
+  g1[i].x += g.x;
+  g1[i].y -= g.y;
+}
+
 __global__ void k_accumulate(float* __restrict__ acc, const float* __restrict__ g, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) acc[i] += g[i];
@@ -609,8 +693,8 @@ __global__ void k_fcg_pupdate(float2* __restrict__ p, const float2* __restrict__
   const float br = restart ? 0.f : (float)(-st->qz[0] / pq), bi = restart ? 0.f : (float)(-st->qz[1] / pq);
   double vr = 0.0, vi = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsite; i += gridDim.x * blockDim.x) {
-    float2 pv[3], zv[3], rv[3];
-    load3(p, i, pv);
+    float2 pv[3] = {}, zv[3], rv[3];
+    if (!restart) load3(p, i, pv);  // a restart never reads p (it may hold stale data)
     load3(z, i, zv);
     load3(r, i, rv);
     float tr = 0.f, ti = 0.f;
@@ -754,6 +838,7 @@ struct hisq_ptc {
   float *m1 = nullptr, *v1 = nullptr, *m2 = nullptr, *v2 = nullptr;
   float2 *g1 = nullptr, *g2 = nullptr;  // gradients
   int adam_t = 0;
+  int tied = 0;  // layer 2 = adjoint of layer 1 (N = B^dag B)
   int* d_err = nullptr;
 };
 
@@ -805,7 +890,7 @@ static int forward_layer(hisq_ptc* P, const float2* in, float2* out, const float
   const int n_out = OUT_EVEN ? c->g.half : c->g.V;
   int grid = launch_tc(c, kern, smem, (n_out + PTC_TILE - 1) / PTC_TILE, "ptc forward");
   if (grid < 0) return grid;
-  kern<<<grid, 128, smem, c->stream>>>(ptc_geom(c), in, out, W, P->d_err, skip);
+  kern<<<grid, 256, smem, c->stream>>>(ptc_geom(c), in, out, W, P->d_err, skip);
   HISQ_CUDA(cudaGetLastError());
   note_launch(c);
   return HISQ_OK;
@@ -952,7 +1037,20 @@ int hisq_ptc_set_weights(hisq_ptc* P, const float* w1, const float* w2) {
   HISQ_CUDA(cudaMemcpyAsync(P->w2, w2, nb, cudaMemcpyDefault, P->ctx->stream));
   HISQ_CUDA(cudaMemsetAsync(P->m1, 0, 4 * nb, P->ctx->stream));
   P->adam_t = 0;
+  if (P->tied) k_tie<<<1, 128, 0, P->ctx->stream>>>(P->w1, P->w2, P->C);
+  HISQ_CUDA(cudaGetLastError());
   HISQ_CUDA(cudaStreamSynchronize(P->ctx->stream));
+  return HISQ_OK;
+}
+
+int hisq_ptc_set_tied(hisq_ptc* P, int tied) {
+  if (!P) return set_error(HISQ_EINVAL, "null network");
+  P->tied = tied ? 1 : 0;
+  if (P->tied) {
+    k_tie<<<1, 128, 0, P->ctx->stream>>>(P->w1, P->w2, P->C);
+    HISQ_CUDA(cudaGetLastError());
+    HISQ_CUDA(cudaStreamSynchronize(P->ctx->stream));
+  }
   return HISQ_OK;
 }
 
@@ -1050,6 +1148,11 @@ int hisq_ptc_train_step(hisq_ptc* P, const float* b, const float* x, int npairs,
   }
   int rc = check_err(P);
   if (rc != HISQ_OK) return rc;
+  if (P->tied) {
+    k_tie_grad<<<1, 128, 0, c->stream>>>(acc1, acc2, C);
+    HISQ_CUDA(cudaGetLastError());
+    note_launch(c);
+  }
   if (loss_out) *loss_out = (float)loss;
   if (g1_out) HISQ_CUDA(cudaMemcpy(g1_out, acc1, (size_t)C * NHOP * sizeof(float2), cudaMemcpyDeviceToHost));
   if (g2_out) HISQ_CUDA(cudaMemcpy(g2_out, acc2, (size_t)C * NHOP * sizeof(float2), cudaMemcpyDeviceToHost));
@@ -1059,7 +1162,10 @@ int hisq_ptc_train_step(hisq_ptc* P, const float* b, const float* x, int npairs,
     const float c1 = 1.f - powf(b1, (float)P->adam_t), c2 = 1.f - powf(b2, (float)P->adam_t);
     const int n = 2 * C * NHOP;
     k_adam<<<1, 256, 0, c->stream>>>((float*)P->w1, P->m1, P->v1, (const float*)acc1, n, lr, b1, b2, 1e-8f, c1, c2);
-    k_adam<<<1, 256, 0, c->stream>>>((float*)P->w2, P->m2, P->v2, (const float*)acc2, n, lr, b1, b2, 1e-8f, c1, c2);
+    if (P->tied)
+      k_tie<<<1, 128, 0, c->stream>>>(P->w1, P->w2, C);
+    else
+      k_adam<<<1, 256, 0, c->stream>>>((float*)P->w2, P->m2, P->v2, (const float*)acc2, n, lr, b1, b2, 1e-8f, c1, c2);
     HISQ_CUDA(cudaGetLastError());
     note_launch(c, 2);
     HISQ_CUDA(cudaStreamSynchronize(c->stream));

@@ -94,7 +94,7 @@ def test_ptc_training_reduces_loss(setup):
     assert last < 0.8 * first, (first, last)
 
 
-@pytest.mark.parametrize("weights", ["identity"])
+@pytest.mark.parametrize("weights", ["identity", "trained"])
 def test_fcg_true_residual(setup, weights):
     import torch
     lat, net, ff, lf = setup
@@ -106,9 +106,11 @@ def test_fcg_true_residual(setup, weights):
         W2[0, 0, 0] = 1.0
         net.set_weights(W1, W2)
     else:
+        # the tied network N = B^dag B is Hermitian positive semi-definite
         W1, W2 = optc.init_weights(41, scale=0.05)
-        W1[0, 0, 0] = W2[0, 0, 0] = 1.0
-        net.set_weights(W1, W2)
+        W1[0, 0, 0] = 1.0
+        net.set_tied(True)
+        net.set_weights(W1, optc.tie(W1))
         bs = hin.gen_source(70, lat.half, 8)
         xs = np.stack([oracle.cg(L, ff, lf, mass, bs[i], tol=1e-8)[0] for i in range(8)])
         bd = torch.from_numpy(bs).to(torch.complex64).cuda()
@@ -122,8 +124,29 @@ def test_fcg_true_residual(setup, weights):
     r = oracle.true_residual(L, ff, lf, mass, b[0], x.cpu().numpy()[0])
     assert r <= 1e-10
     assert abs(r - st["true_rel_residual"]) < 1e-11
+    net.set_tied(False)
     if weights == "identity":
         # identity preconditioner: FCG takes about as many iterations as CG
         xc = torch.zeros_like(x)
         _, sc = lat.cg(xc, torch.from_numpy(b).cuda(), mass, 1e-10, 3000, inner_prec=1)
         assert abs(st["iters"] - sc["iters"]) <= 0.15 * sc["iters"] + 5
+
+
+def test_ptc_tied_gradient_parity(setup):
+    import torch
+    lat, net, ff, lf = setup
+    W1, _ = optc.init_weights(51)
+    net.set_tied(True)
+    net.set_weights(W1, optc.tie(W1))
+    bs = hin.gen_source(52, lat.half, 2)
+    xs = hin.gen_source(53, lat.half, 2)
+    bd = torch.from_numpy(bs).to(torch.complex64).cuda()
+    xd = torch.from_numpy(xs).to(torch.complex64).cuda()
+    loss, g1, _ = net.train_step(bd, xd, 2, 0.0)
+    a, b = net.get_weights()
+    net.set_tied(False)
+    w1 = W1.astype(np.complex64).astype(np.complex128)
+    assert np.allclose(b, optc.tie(w1).astype(np.complex64))  # layer 2 follows layer 1
+    rloss, G = optc.loss_and_grads_tied(L, ff, w1, list(bs), list(xs))
+    assert abs(loss - rloss) <= 1e-2 * abs(rloss)
+    assert rel(g1.astype(np.complex128), G) <= 2e-2, rel(g1, G)

@@ -119,3 +119,40 @@ def test_input_gradient_finite_differences(fat):
             fd = (loss(pp) - loss(pm)) / (2 * eps)
             an = 2 * (np.conj(g_in[idx]) * d).real
             assert abs(fd - an) <= 1e-8 * max(1.0, abs(an))
+
+
+def test_tied_network_is_hermitian_psd():
+    fat, _ = folded(L, seed=99)
+    W1, _ = ptc.init_weights(8)
+    W2 = ptc.tie(W1)
+    rng = np.random.default_rng(12)
+    n = oracle.volume(L) // 2
+    u, v = random_vec(rng, n), random_vec(rng, n)
+    Nu, _ = ptc.network_forward(L, fat, W1, W2, u)
+    Nv, _ = ptc.network_forward(L, fat, W1, W2, v)
+    assert abs(np.vdot(u, Nv) - np.conj(np.vdot(v, Nu))) < 1e-12 * abs(np.vdot(u, Nv))
+    assert np.vdot(v, Nv).real > 0 and abs(np.vdot(v, Nv).imag) < 1e-12 * np.vdot(v, Nv).real
+    # N v = B^dag B v: <v, N v> equals the squared norm of the layer-1 output
+    psi1 = ptc.layer_forward(L, fat, W1, oracle.to_full(L, even=v)[None])
+    assert abs(np.vdot(v, Nv).real - np.vdot(psi1, psi1).real) < 1e-10 * np.vdot(psi1, psi1).real
+
+
+def test_tied_gradient_finite_differences():
+    fat, _ = folded(L, seed=101)
+    W1, _ = ptc.init_weights(9)
+    n = oracle.volume(L) // 2
+    bs = list(hin.gen_source(31, n, 2))
+    xs = list(hin.gen_source(32, n, 2))
+    loss, G = ptc.loss_and_grads_tied(L, fat, W1, bs, xs)
+    rng = np.random.default_rng(13)
+    eps = 1e-6
+    for _ in range(6):
+        idx = tuple(int(rng.integers(0, s)) for s in W1.shape)
+        for d in (1.0, 1j):
+            Wp, Wm = W1.copy(), W1.copy()
+            Wp[idx] += eps * d
+            Wm[idx] -= eps * d
+            fd = (ptc.loss_and_grads_tied(L, fat, Wp, bs, xs)[0] - ptc.loss_and_grads_tied(L, fat, Wm, bs, xs)[0]) / (
+                2 * eps)
+            an = 2 * (np.conj(G[idx]) * d).real
+            assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (idx, d, fd, an)
