@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the steps only: no e2e, comparison solves or CPU baseline (for profiler launch lists)")
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
+    ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-f16", "dslash-f32-comp", "ptc", "batch"],
+                    help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
     return ap.parse_args()
@@ -336,12 +338,28 @@ def run_ours(args, rank, world, local):
         for name, o in (("mixed_f32", dict(inner_prec=h.HISQ_F32)), ("mixed_f16", dict(inner_prec=h.HISQ_F16)),
                         ("fp64", dict(inner_prec=h.HISQ_F64))):
             xs = torch.zeros_like(b)
+            lat.cg(xs, b, m, TOL, 20000, **o)  # first call tunes this variant's kernels
+            xs.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             rc, st = lat.cg(xs, b, m, TOL, 20000, **o)
             dt = time.perf_counter() - t0
             row[name] = {"s": round(dt, 4), "iters": st["iters"], "true_res": st["true_rel_residual"]}
         cmp["m=%g" % m] = row
+    # the same solves with compressed long links (two rows stored, third rebuilt in the kernel)
+    lat.compress_long(-1.0 / 24.0).load(fat, lng)
+    for m in (0.01, 0.002):
+        for name, o in (("mixed_f32_comp12", dict(inner_prec=h.HISQ_F32)),
+                        ("mixed_f16_comp12", dict(inner_prec=h.HISQ_F16))):
+            xs = torch.zeros_like(b)
+            lat.cg(xs, b, m, TOL, 20000, **o)  # first call tunes the compressed kernels
+            xs.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = lat.cg(xs, b, m, TOL, 20000, **o)
+            dt = time.perf_counter() - t0
+            cmp["m=%g" % m][name] = {"s": round(dt, 4), "iters": st["iters"], "true_res": st["true_rel_residual"]}
+    ms_comp = time_dslash(torch, lat, h.HISQ_F32, 1, reps, stream)
 
     if rank != 0:
         if dist:
@@ -367,6 +385,7 @@ def run_ours(args, rank, world, local):
                      "frac": round(achieved / peak, 4), "peak_source": peak_src,
                      "kernel": "dslash_kernel<float,float,1,EPI_PLAIN> 48^3x12",
                      "us_per_launch": round(ms_launch * 1e3, 2), "bytes_per_launch": bytes_launch,
+                     "us_per_launch_compressed_long_links": round(ms_comp * 1e3, 2),
                      "traffic": ncu_traffic("ncu_dslash_f32_48c12.txt")},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_bytes / t_e2e / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": 2 * vec_bytes,
@@ -586,6 +605,54 @@ def run_row(name):
      "learned": row_learned}[name](h, torch, hin)
 
 
+def run_kernel_case(name):
+    """A handful of launches of one kernel on a modest case (inputs larger than L2), for ncu."""
+    import torch
+
+    import __graft_entry__
+    import hisq_inputs as hin
+    __graft_entry__.build()
+    import paper_2111_10354_gb300 as h
+    stream = torch.cuda.Stream()
+    if name.startswith("dslash"):
+        L = (48, 48, 48, 12)
+        fat, lng = hin.gen_links(L, 1001, 0.3, 0.1)
+        lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16), stream=stream)
+        if name == "dslash-f32-comp":
+            lat.compress_long(-1.0 / 24.0)
+        lat.load(fat, lng)
+        prec = {"dslash-f64": h.HISQ_F64, "dslash-f16": h.HISQ_F16, "dslash-f32-comp": h.HISQ_F32}[name]
+        ms = time_dslash(torch, lat, prec, 1, 4, stream)
+        print(json.dumps({"case": name, "us": round(ms * 1e3, 2)}))
+    elif name == "ptc":
+        import oracle.ptc as optc
+        L = (32, 32, 32, 8)
+        fat, lng = hin.gen_links(L, 4000, 0.35, 0.1)
+        lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=stream).load(fat, lng)
+        net = h.Ptc(lat)
+        W1, _ = optc.init_weights(4000, scale=0.05)
+        net.set_tied(True)
+        net.set_weights(W1, optc.tie(W1))
+        r = torch.from_numpy(hin.gen_source(1, lat.half, 1)).to(torch.complex64).cuda()
+        z = torch.empty_like(r)
+        for _ in range(4):
+            net.apply(z, r, 1)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "ok": True}))
+    elif name == "batch":
+        mix = hin.lattice_mix_64()[:16] + hin.lattice_mix_64()[32:40] + hin.lattice_mix_64()[51:55]
+        batch = h.Batch([m["dims"] for m in mix], stream=stream)
+        bs = []
+        for l, m in enumerate(mix):
+            fat, lng = hin.gen_links(m["dims"], m["gauge_seed"], m["eps"], 0.1)
+            batch.load(l, fat, lng)
+            bs.append(hin.gen_source(m["source_seed"], int(np.prod(m["dims"])) // 2, 1)[0])
+        b = torch.from_numpy(np.concatenate([v.reshape(-1) for v in bs]).reshape(-1, 3)).cuda()
+        x = torch.zeros_like(b)
+        rc, st = batch.cg(x, b, [m["mass"] for m in mix], 1e-10, 10000, inner_prec=h.HISQ_F32)
+        print(json.dumps({"case": name, "iters": st["iters"]}))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -596,6 +663,9 @@ def main():
         return
     if args.row:
         run_row(args.row)
+        return
+    if args.kernel_case:
+        run_kernel_case(args.kernel_case)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

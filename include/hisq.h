@@ -287,6 +287,17 @@ int hisq_fcg(hisq_ctx* ctx, hisq_ptc* ptc, double* x, const double* b, double ma
  */
 int hisq_apply_A_noalloc(hisq_ctx* ctx, void* out, const void* in, double mass, double sigma, int prec, int nrhs);
 
+/*
+ * Rational function of A applied to a vector, as RHMC uses the multi-shift CG (Sec. 2: RHMC for
+ * HISQ fermions; Sec. 3: multi-shift CG): out = a0 b + sum_k coeffs[k] (A + shifts[k])^-1 b, each
+ * shifted system solved to rel_tol[k] by hisq_multishift_cg (same options). The coefficients of a
+ * rational approximation are the caller's (the paper gives none). out, b: complex128 [V/2][3],
+ * host or device. stats: those of the multi-shift solve.
+ */
+int hisq_rational_apply(hisq_ctx* ctx, double* out, const double* b, double a0, int nshift, const double* shifts,
+                        const double* coeffs, double mass, const double* rel_tol, int maxiter,
+                        const hisq_solver_opts* opts, hisq_solver_stats* stats);
+
 /* ---------------------------------------------------------------- diagnostics */
 const char* hisq_strerror(int code);
 const char* hisq_last_error(void);

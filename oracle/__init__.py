@@ -192,3 +192,14 @@ def to_full(L, even=None, odd=None):
 
 def from_full(L, full, p: int):
     return np.ascontiguousarray(full[parity_sites(L, p)])
+
+
+def rational_apply(L, fat, lng, mass: float, b, a0: float, coeffs, sigmas, tol=1e-12, maxiter: int = 10000):
+    """r(A) b = a0 b + sum_k a_k (A + sigma_k)^-1 b: the rational-function use of the multi-shift CG
+    in RHMC (Sec. 2: RHMC for HISQ fermions; Sec. 3: multi-shift CG). Coefficients are inputs."""
+    b = _c(b)
+    xs, its, _ = multishift_cg(L, fat, lng, mass, sigmas, b, tol, maxiter)
+    out = a0 * b
+    for a, x in zip(coeffs, xs):
+        out = out + a * x
+    return out

@@ -108,6 +108,8 @@ def _load():
     lib.hisq_batch_launch_count.restype = ctypes.c_longlong
     lib.hisq_batch_cg.argtypes = [vp, vp, vp, vp, dp, ip, ctypes.POINTER(hisq_solver_opts),
                                   ctypes.POINTER(hisq_solver_stats), vp, vp]
+    lib.hisq_rational_apply.argtypes = [vp, vp, vp, dp, ip, vp, vp, dp, vp, ip, ctypes.POINTER(hisq_solver_opts),
+                                        ctypes.POINTER(hisq_solver_stats)]
     fp = ctypes.c_float
     lib.hisq_ptc_create.argtypes = [ctypes.POINTER(vp), vp, ip]
     lib.hisq_ptc_destroy.argtypes = [vp]
@@ -243,6 +245,19 @@ def hisq_multishift_cg(ctx, x, b, shifts, mass: float, rel_tol, maxiter: int, op
     if rc != HISQ_OK and raise_on_error:
         raise HisqError(rc, "hisq_multishift_cg", hisq_last_error(), d)
     return rc, d
+
+
+def hisq_rational_apply(ctx, out, b, a0: float, shifts, coeffs, mass: float, rel_tol, maxiter: int, opts=None):
+    """out = a0 b + sum_k coeffs[k] (A + shifts[k])^-1 b; returns the multi-shift stats."""
+    shifts = np.ascontiguousarray(shifts, dtype=np.float64)
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    ns = len(shifts)
+    tols = np.ascontiguousarray(np.broadcast_to(np.asarray(rel_tol, np.float64), (ns,)))
+    st = hisq_solver_stats()
+    o = opts if opts is not None else hisq_solver_opts_default()
+    _check(_load().hisq_rational_apply(ctx, _ptr(out), _ptr(b), a0, ns, _ptr(shifts), _ptr(coeffs), mass, _ptr(tols),
+                                       maxiter, ctypes.byref(o), ctypes.byref(st)), "hisq_rational_apply")
+    return st.as_dict()
 
 
 def hisq_dslash_bytes(ctx, prec: int, nrhs: int = 1) -> float:

@@ -836,6 +836,22 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
   return run_cg<float>(ctx, x, b, 0, ns, mass, shifts, tol, remaining, o, stats);
 }
 
+// out = a0 b + sum_k a_k x_k (FP64), one pass over b and the nshift solutions.
+__global__ void k_rational_combine(double2* __restrict__ out, const double2* __restrict__ b,
+                                   const double2* __restrict__ x, size_t n, int ns, double a0,
+                                   const double* __restrict__ coeffs) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 bv = b[i];
+    double re = a0 * bv.x, im = a0 * bv.y;
+    for (int k = 0; k < ns; ++k) {
+      const double2 xv = x[(size_t)k * n + i];
+      re += coeffs[k] * xv.x;
+      im += coeffs[k] * xv.y;
+    }
+    out[i] = make_double2(re, im);
+  }
+}
+
 }  // namespace hisq
 
 using namespace hisq;
@@ -934,6 +950,38 @@ int hisq_multishift_cg(hisq_ctx* ctx, double* x, const double* b, int nshift, co
     rc = run_multishift<float>(ctx, s.x, s.b, nshift, shifts, mass, rel_tol, maxiter, o, stats);
   if (stats) stats->kernel_launches = ctx->launches - l0;
   return unstage(ctx, x, (size_t)nshift * n * sizeof(double2), s, rc);
+}
+
+
+int hisq_rational_apply(hisq_ctx* ctx, double* out, const double* b, double a0, int nshift, const double* shifts,
+                        const double* coeffs, double mass, const double* rel_tol, int maxiter,
+                        const hisq_solver_opts* opts, hisq_solver_stats* stats) {
+  if (!ctx || !out || !b || !coeffs || !shifts || !rel_tol) return set_error(HISQ_EINVAL, "null argument");
+  if (nshift < 1 || nshift > MAXR) return set_error(HISQ_EINVAL, "nshift %d outside [1, %d]", nshift, MAXR);
+  if ((uintptr_t)out % 16) return set_error(HISQ_EINVAL, "vectors must be 16-byte aligned");
+  const size_t n = (size_t)ctx->g.half * 3;
+  double2* xs = (double2*)workspace(ctx, "rat_x", (size_t)nshift * n * sizeof(double2));
+  double* dc = (double*)workspace(ctx, "rat_coeffs", MAXR * sizeof(double));
+  if (!xs || !dc) return set_error(HISQ_ENOMEM, "rational workspace");
+  int rc = hisq_multishift_cg(ctx, (double*)xs, b, nshift, shifts, mass, rel_tol, maxiter, opts, stats);
+  if (rc != HISQ_OK) return rc;
+  const bool bh = !is_device_ptr(b), oh = !is_device_ptr(out);
+  const double2* db = (const double2*)b;
+  if (bh) {
+    double2* t = (double2*)workspace(ctx, "user_b", n * sizeof(double2));
+    if (!t) return set_error(HISQ_ENOMEM, "staging");
+    HISQ_CUDA(cudaMemcpyAsync(t, b, n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    db = t;
+  }
+  double2* dout = oh ? (double2*)workspace(ctx, "rat_out", n * sizeof(double2)) : (double2*)out;
+  if (!dout) return set_error(HISQ_ENOMEM, "staging");
+  HISQ_CUDA(cudaMemcpyAsync(dc, coeffs, nshift * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  k_rational_combine<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(dout, db, xs, n, nshift, a0, dc);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx);
+  if (oh) HISQ_CUDA(cudaMemcpyAsync(out, dout, n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HISQ_OK;
 }
 
 }  // extern "C"

@@ -165,33 +165,48 @@ __device__ __forceinline__ void put_bf16(unsigned char* tile, int row, int col, 
 // out_a(x) = sum_{b,h} W[a][b][h] T_h in_b (x). in: [CIN][V][3] float2 (full lattice);
 // out: [COUT][n_out][3] float2 with n_out = V (full) or V/2 (even sites, cb order).
 // W: [COUT][CIN][9] float2 (FP32 master weights, rounded to BF16 for the tensor cores).
+// Feature order is hop-major, k = h * CIN + b: with CIN = 8 each hop fills exactly one 16-column
+// MMA K-step, so the operand tile can be staged a few hops at a time (HPP hops per pass, all
+// passes accumulating into the same TMEM tile), which keeps the shared-memory footprint small
+// enough for several CTAs per SM to overlap their fill, MMA and read-out phases.
+template <int CIN>
+struct FwdShape {
+  static constexpr int HPP = CIN == 8 ? 3 : NHOP;                        // hops per pass
+  static constexpr int NPASS = (NHOP + HPP - 1) / HPP;
+  static constexpr int K2A = ((2 * CIN * HPP + 15) / 16) * 16;           // A columns per pass
+  static constexpr int K2B = CIN == 8 ? 2 * CIN * NHOP : K2A;            // B columns (all hops)
+};
+
 template <int CIN, int COUT, bool OUT_EVEN>
 __global__ void __launch_bounds__(256) k_ptc_forward(const PtcGeom G, const float2* __restrict__ in,
                                                      float2* __restrict__ out, const float2* __restrict__ W,
                                                      int* err, const int* skip) {
   if (skip && *skip) return;  // a solver cycle that has already finished (uniform)
-  constexpr int K2 = ((2 * NHOP * CIN + 15) / 16) * 16;
+  using S = FwdShape<CIN>;
+  constexpr int K2A = S::K2A, K2B = S::K2B, HPP = S::HPP, NPASS = S::NPASS;
   constexpr int N2 = ((2 * COUT + 15) / 16) * 16;
   constexpr int TM_COLS = (3 * N2 <= 32) ? 32 : (3 * N2 <= 64) ? 64 : (3 * N2 <= 128) ? 128 : 256;
+  static_assert(CIN == 1 || CIN == 8, "layer shapes of the network");
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* A = smem;                              // 3 colours x [128 x K2] bf16
-  unsigned char* B = smem + 3 * PTC_TILE * K2 * 2;      // [N2 x K2] bf16
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(B + N2 * K2 * 2);
+  unsigned char* A = smem;                               // 3 colours x [128 x K2A] bf16
+  unsigned char* B = smem + 3 * PTC_TILE * K2A * 2;      // [N2 x K2B] bf16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(B + N2 * K2B * 2);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const Geom& g = G.g;
 
-  // zero both operand tiles (padding rows/columns stay zero), weights -> B
-  for (int i = tid; i < (3 * PTC_TILE * K2 + N2 * K2) / 8; i += blockDim.x)
+  for (int i = tid; i < (3 * PTC_TILE * K2A + N2 * K2B) / 8; i += blockDim.x)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   __syncthreads();
+  // B[n][k]: k = 2*(h*CIN + b) + {re, im}; n = 2a + {re, im}; complex weight as a 2x2 real block
   for (int i = tid; i < COUT * CIN * NHOP; i += blockDim.x) {
-    const int a = i / (CIN * NHOP), k = i % (CIN * NHOP);  // k = b*9 + h
+    const int a = i / (CIN * NHOP), b = (i / NHOP) % CIN, h = i % NHOP;  // W[a][b][h]
     const float2 w = W[i];
-    put_bf16(B, 2 * a, 2 * k, K2, w.x);
-    put_bf16(B, 2 * a, 2 * k + 1, K2, -w.y);
-    put_bf16(B, 2 * a + 1, 2 * k, K2, w.y);
-    put_bf16(B, 2 * a + 1, 2 * k + 1, K2, w.x);
+    const int k = h * CIN + b;
+    put_bf16(B, 2 * a, 2 * k, K2B, w.x);
+    put_bf16(B, 2 * a, 2 * k + 1, K2B, -w.y);
+    put_bf16(B, 2 * a + 1, 2 * k, K2B, w.y);
+    put_bf16(B, 2 * a + 1, 2 * k + 1, K2B, w.x);
   }
   if (tid == 0) tc::mbar_init(tc::smem_addr(mbar), 1);
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(tslot), TM_COLS);
@@ -206,48 +221,55 @@ __global__ void __launch_bounds__(256) k_ptc_forward(const PtcGeom G, const floa
   bool failed = false;
 
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    // fill: work item = (row, hop); consecutive threads take consecutive sites
-    for (int item = tid; item < PTC_TILE * NHOP; item += blockDim.x) {
-      const int row = item % PTC_TILE, h = item / PTC_TILE;
-      int c[4], idx, oi;
-      cplx<float> u[CIN][3];
-      if (tile_site(g, OUT_EVEN, tile, row, c, &idx, &oi)) {
-        transport_multi<CIN>(G, in, c, idx, h, u);
-      } else {
+#pragma unroll 1
+    for (int pass = 0; pass < NPASS && !failed; ++pass) {
+      const int h0 = pass * HPP;
+      const int nh = (NHOP - h0) < HPP ? (NHOP - h0) : HPP;
+      // fill this pass's hops: work item = (row, hop); consecutive threads take consecutive sites
+      for (int item = tid; item < PTC_TILE * nh; item += blockDim.x) {
+        const int row = item % PTC_TILE, hl = item / PTC_TILE, h = h0 + hl;
+        int c[4], idx, oi;
+        cplx<float> u[CIN][3];
+        if (tile_site(g, OUT_EVEN, tile, row, c, &idx, &oi)) {
+          transport_multi<CIN>(G, in, c, idx, h, u);
+        } else {
 #pragma unroll
-        for (int b = 0; b < CIN; ++b)
+          for (int b = 0; b < CIN; ++b)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) u[b][k] = {0.f, 0.f};
+            for (int k = 0; k < 3; ++k) u[b][k] = {0.f, 0.f};
+        }
+#pragma unroll
+        for (int b = 0; b < CIN; ++b) {
+          const int k = hl * CIN + b;
+#pragma unroll
+          for (int col = 0; col < 3; ++col)
+            put_bf16x2(A + col * PTC_TILE * K2A * 2, row, 2 * k, K2A, u[b][col].re, u[b][col].im);
+        }
       }
-#pragma unroll
-      for (int b = 0; b < CIN; ++b) {
-        const int k = b * NHOP + h;
-#pragma unroll
-        for (int col = 0; col < 3; ++col)
-          put_bf16x2(A + col * PTC_TILE * K2 * 2, row, 2 * k, K2, u[b][col].re, u[b][col].im);
+      tc::fence_smem_to_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        const int ksteps = CIN == 8 ? nh : K2A / 16;
+#pragma unroll 1
+        for (int col = 0; col < 3; ++col) {
+          const uint32_t a0 = tc::smem_addr(A + col * PTC_TILE * K2A * 2), b0 = tc::smem_addr(B);
+#pragma unroll 1
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const int kb = CIN == 8 ? (h0 + ks) : ks;  // K-step of B (a hop for CIN = 8)
+            tc::mma_bf16(tmem + col * N2, tc::desc_kmajor(a0 + ks * 256, K2A), tc::desc_kmajor(b0 + kb * 256, K2B),
+                         idesc, (pass > 0 || ks > 0) ? 1u : 0u);
+          }
+        }
+        tc::commit(tc::smem_addr(mbar));
       }
-    }
-    tc::fence_smem_to_async();
-    __syncthreads();
-    if (tid == 0) {
+      // the next pass (or tile) overwrites A: wait until the tensor core has read it
+      const bool ok = tc::mbar_wait(tc::smem_addr(mbar), phase, WAIT_LIMIT);
+      phase ^= 1;
+      if (__syncthreads_or(!ok)) failed = true;
       tc::fence_after_sync();
-#pragma unroll 1
-      for (int col = 0; col < 3; ++col) {
-        const uint32_t a0 = tc::smem_addr(A + col * PTC_TILE * K2 * 2), b0 = tc::smem_addr(B);
-#pragma unroll 1
-        for (int ks = 0; ks < K2 / 16; ++ks)
-          tc::mma_bf16(tmem + col * N2, tc::desc_kmajor(a0 + ks * 256, K2), tc::desc_kmajor(b0 + ks * 256, K2), idesc,
-                       ks > 0);
-      }
-      tc::commit(tc::smem_addr(mbar));
     }
-    const bool ok = tc::mbar_wait(tc::smem_addr(mbar), phase, WAIT_LIMIT);
-    phase ^= 1;
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    tc::fence_after_sync();
+    if (failed) break;
     // readout: warp w reads TMEM lanes 32*(w%4).. (rows) for colours w/4, w/4 + 2, ...
     {
       const int q = warp & 3, row = 32 * q + (tid & 31);
@@ -854,8 +876,8 @@ static PtcGeom ptc_geom(const hisq_ctx* c) {
 
 template <int CIN, int COUT>
 static size_t fwd_smem() {
-  constexpr int K2 = ((2 * NHOP * CIN + 15) / 16) * 16, N2 = ((2 * COUT + 15) / 16) * 16;
-  return (size_t)3 * PTC_TILE * K2 * 2 + (size_t)N2 * K2 * 2 + 16;
+  constexpr int N2 = ((2 * COUT + 15) / 16) * 16;
+  return (size_t)3 * PTC_TILE * FwdShape<CIN>::K2A * 2 + (size_t)N2 * FwdShape<CIN>::K2B * 2 + 16;
 }
 template <int CIN, int COUT>
 static size_t mix_smem() {
@@ -890,6 +912,24 @@ static int forward_layer(hisq_ptc* P, const float2* in, float2* out, const float
   const int n_out = OUT_EVEN ? c->g.half : c->g.V;
   int grid = launch_tc(c, kern, smem, (n_out + PTC_TILE - 1) / PTC_TILE, "ptc forward");
   if (grid < 0) return grid;
+  // several CTAs per SM: as many as registers, shared memory and threads allow, and at most 6
+  // (each holds 64 TMEM columns; 8 would fill the SM's 512)
+  static int per_sm = 0;
+  if (per_sm == 0 && !c->capturing) {
+    cudaFuncAttributes fa;
+    int dev = 0, smem_sm = 0;
+    HISQ_CUDA(cudaFuncGetAttributes(&fa, (const void*)kern));
+    HISQ_CUDA(cudaGetDevice(&dev));
+    HISQ_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const int by_regs = 65536 / ((fa.numRegs > 0 ? fa.numRegs : 64) * 256);
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    per_sm = by_regs < by_smem ? by_regs : by_smem;
+    if (per_sm > 6) per_sm = 6;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int ntiles = (n_out + PTC_TILE - 1) / PTC_TILE;
+  grid = c->num_sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > ntiles) grid = ntiles;
   kern<<<grid, 256, smem, c->stream>>>(ptc_geom(c), in, out, W, P->d_err, skip);
   HISQ_CUDA(cudaGetLastError());
   note_launch(c);

@@ -79,3 +79,22 @@ def test_multishift_errors(hisq):
     with pytest.raises(hisq.HisqError) as e:
         lat.multishift_cg(x, b, [0.1, 0.2], 0.1, 1e-8, 100, inner_prec=1)  # FP32 links not resident
     assert e.value.code == hisq.HISQ_EINVAL
+
+
+@pytest.mark.parametrize("inner", [0, 1])
+def test_rational_apply(hisq, inner):
+    """RHMC's rational apply r(A) b = a0 b + sum_k a_k (A + s_k)^-1 b against the oracle's composition."""
+    import torch
+    L = (8, 10, 12, 14)
+    mass = 0.01
+    fat, lng = hin.gen_links(L, 321, 0.3, 0.1)
+    lat = hisq.Lattice(L, precs=(0, 1)).load(fat, lng)
+    ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
+    b = hin.gen_source(322, lat.half, 1)[0]
+    a0, coeffs, shifts = 0.25, [0.9, 0.4, 0.1, 0.05], [1e-4, 1e-2, 0.3, 2.0]
+    out = torch.empty((lat.half, 3), dtype=torch.complex128, device="cuda")
+    st = hisq.hisq_rational_apply(lat.ctx, out, torch.from_numpy(b).cuda(), a0, shifts, coeffs, mass, 1e-11, 5000,
+                                  hisq.make_opts(inner_prec=inner))
+    assert st["converged"] == 1
+    ref = oracle.rational_apply(L, ff, lf, mass, b, a0, coeffs, shifts, tol=1e-13)
+    assert np.linalg.norm(out.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-8

@@ -92,3 +92,20 @@ def test_multishift_matches_single_shift():
         assert r < 1e-9
         xk, _ = oracle.cg(L, fat, lng, mass, b, tol=1e-12, sigma=s)
         assert np.linalg.norm(xs[k] - xk) / np.linalg.norm(xk) < 1e-7
+
+
+def test_rational_apply_matches_eigendecomposition():
+    """Closed form on 4^4: r(A) b = V diag(a0 + sum_k a_k / (lambda + sigma_k)) V^dag b from a dense
+    eigendecomposition of the oracle's A (numpy), against the multi-shift route."""
+    from test_oracle_dslash import dense_A
+    L = (4, 4, 4, 4)
+    mass = 0.05
+    fat, lng = folded(L, seed=1234)
+    A = dense_A(L, fat, lng, mass)
+    lam, V = np.linalg.eigh(A)
+    b = hin.gen_source(55, oracle.volume(L) // 2)[0]
+    a0, coeffs, sigmas = 0.3, [0.5, 0.2, 1.1], [0.01, 0.2, 1.5]
+    f = a0 + sum(a / (lam + s) for a, s in zip(coeffs, sigmas))
+    ref = (V @ (f * (V.conj().T @ b.ravel()))).reshape(-1, 3)
+    got = oracle.rational_apply(L, fat, lng, mass, b, a0, coeffs, sigmas, tol=1e-13)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
