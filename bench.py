@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the steps only: no e2e, comparison solves or CPU baseline (for profiler launch lists)")
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
-    ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-f16", "dslash-f32-comp", "ptc", "batch"],
+    ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8", "ptc", "batch"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
@@ -621,8 +621,9 @@ def run_kernel_case(name):
         if name == "dslash-f32-comp":
             lat.compress_long(-1.0 / 24.0)
         lat.load(fat, lng)
-        prec = {"dslash-f64": h.HISQ_F64, "dslash-f16": h.HISQ_F16, "dslash-f32-comp": h.HISQ_F32}[name]
-        ms = time_dslash(torch, lat, prec, 1, 4, stream)
+        prec = {"dslash-f64": h.HISQ_F64, "dslash-f16": h.HISQ_F16, "dslash-f32-comp": h.HISQ_F32,
+                "dslash-f32-nr8": h.HISQ_F32}[name]
+        ms = time_dslash(torch, lat, prec, 8 if name.endswith("nr8") else 1, 4, stream)
         print(json.dumps({"case": name, "us": round(ms * 1e3, 2)}))
     elif name == "ptc":
         import oracle.ptc as optc

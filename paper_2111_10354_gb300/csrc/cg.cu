@@ -57,6 +57,42 @@ __global__ void k_residual(const double2* __restrict__ b, size_t b_stride, const
   }
 }
 
+// |x_r|^2 per rhs into out[r] (detects a zero initial guess, whose residual is b itself).
+__global__ void k_xnorm(const double2* __restrict__ x, size_t n, int nrhs, double* partials, size_t pstride,
+                        unsigned* counter, double* out) {
+  const int rh = blockIdx.y;
+  const size_t off = (size_t)rh * n;
+  double v[1] = {0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 xv = x[off + i];
+    v[0] += xv.x * xv.x + xv.y * xv.y;
+  }
+  double o[1][MAXR];
+  if (grid_reduce<1>(v, partials, pstride, counter, o, nrhs) && threadIdx.x == 0)
+    for (int q = 0; q < nrhs; ++q) out[q] = o[0][q];
+}
+
+// r = b (zero initial guess): rr_true = bb = |b|^2 without applying A.
+__global__ void k_residual_zero(const double2* __restrict__ b, size_t b_stride, double2* __restrict__ r, size_t n,
+                                SolverState* st, double* partials, size_t pstride, unsigned* counter) {
+  const int rh = blockIdx.y;
+  const size_t off = (size_t)rh * n;
+  const double2* bq = b + (size_t)rh * b_stride;
+  double v[1] = {0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 bv = bq[i];
+    r[off + i] = bv;
+    v[0] += bv.x * bv.x + bv.y * bv.y;
+  }
+  double o[1][MAXR];
+  if (grid_reduce<1>(v, partials, pstride, counter, o, st->nrhs) && threadIdx.x == 0)
+    for (int q = 0; q < st->nrhs; ++q) {
+      st->rr_true[q] = o[0][q];
+      st->bb[q] = o[0][q];
+      if (!isfinite(o[0][q])) st->nonfinite = 1;
+    }
+}
+
 // Reliable update: for each rhs not yet verified, r_lo = r_hi / s (s = RMS entry of r_hi),
 // p = r_lo (restart); rr = |r_hi|^2 / s^2. Verified rhs are frozen.
 template <typename S>
@@ -364,10 +400,27 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   hst->cycle_limit = mixed ? o.reliable_period : o.poll_every;
   for (int q = 0; q < nrhs; ++q) hst->scale[q] = 1.0;
   HISQ_CUDA(cudaMemcpyAsync(B.st, hst, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
-  int rc = true_residual(ctx, B, nrhs, 1);
-  if (rc != HISQ_OK) return rc;
-  dcalls += 2;
-  dbytes += 2 * dslash_bytes(ctx, HISQ_F64, HISQ_F64, nrhs);
+  // a zero initial guess (the usual start) needs no A x: its residual is b
+  double* xn = (double*)ctx->pinned + 4096;
+  k_xnorm<<<blas_grid(ctx, nrhs, n), 256, 0, ctx->stream>>>(x, n, nrhs, B.partials, partial_stride(ctx),
+                                                             ctx->d_counters + 10, (double*)B.Ax);
+  HISQ_CUDA(cudaGetLastError());
+  HISQ_CUDA(cudaMemcpyAsync(xn, B.Ax, nrhs * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  note_launch(ctx);
+  bool x_zero = true;
+  for (int q = 0; q < nrhs; ++q) x_zero = x_zero && xn[q] == 0.0;
+  int rc;
+  if (x_zero) {
+    k_residual_zero<<<blas_grid(ctx, nrhs), 256, 0, ctx->stream>>>(B.b, B.b_stride, B.r_hi, n, B.st, B.partials,
+                                                                    partial_stride(ctx), ctx->d_counters + 1);
+    HISQ_CUDA(cudaGetLastError());
+    note_launch(ctx);
+  } else {
+    if ((rc = true_residual(ctx, B, nrhs, 1)) != HISQ_OK) return rc;
+    dcalls += 2;
+    dbytes += 2 * dslash_bytes(ctx, HISQ_F64, HISQ_F64, nrhs);
+  }
   HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
   HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
   for (int q = 0; q < nrhs; ++q) {
