@@ -444,13 +444,22 @@ def _timed(torch, fn):
 
 
 def row_multirhs(h, torch, hin):
-    """48^3x12, FP32 storage: Dslash and mixed CG with 1, 4, 8, 16 sources per link read."""
+    """48^3x12: Dslash with 1-16 vectors per link read (FP16, FP64, FP32) and FP32 mixed CG on 1-16 sources."""
     L = (48, 48, 48, 12)
     fat, lng = hin.gen_links(L, 1002, 0.3, 0.1)
     stream = torch.cuda.Stream()
-    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=stream).load(fat, lng)
+    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16), stream=stream).load(fat, lng)
     peak, _ = peaks()
-    for n in (1, 4, 8, 16):
+    # Dslash only at FP16 storage (FP32 arithmetic) and FP64
+    for prec, name, ns in ((h.HISQ_F16, "f16", (1, 2, 4, 8, 16)), (h.HISQ_F64, "f64", (1, 2, 4, 8))):
+        for n in ns:
+            ms = time_dslash(torch, lat, prec, n, 20 if prec != h.HISQ_F64 else 5, stream)
+            by = lat.dslash_bytes(prec, n)
+            print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": name, "nrhs": n,
+                              "dslash_us": round(ms * 1e3, 1), "dslash_GBps": round(by / ms / 1e6, 1),
+                              "dslash_frac_hbm": round(by / ms / 1e6 / peak, 3),
+                              "dslash_GFLOPs": round(1146 * n * lat.half / (ms * 1e-3) / 1e9, 1)}), flush=True)
+    for n in (1, 2, 4, 8, 16):
         ms = time_dslash(torch, lat, h.HISQ_F32, n, 20, stream)
         by = lat.dslash_bytes(h.HISQ_F32, n)
         b = torch.from_numpy(hin.gen_source(2002, lat.half, n)).cuda()
@@ -464,6 +473,8 @@ def row_multirhs(h, torch, hin):
                           "dslash_GFLOPs": round(1146 * n * lat.half / (ms * 1e-3) / 1e9, 1),
                           "cg_s": round(dt, 4), "cg_s_per_rhs": round(dt / n, 4), "cg_iters": st["iters"],
                           "worst_true_res": st["true_rel_residual"]}), flush=True)
+    # launch forms the tuner chose: key -> variant * 10000 + block (vectors per thread x threads per site)
+    print(json.dumps({"row": "multirhs", "tuned": h.hisq_tune_report(lat.ctx).splitlines()}), flush=True)
 
 
 def row_multishift(h, torch, hin):

@@ -4,8 +4,8 @@
 //                   + L_mu(x) in(x+3mu) - L_mu(x-3mu)^dag in(x-3mu) ]
 // with staggered phases and the antiperiodic-t sign already folded into F and L.
 //
-// Design: one thread per output site (grid-stride), NR right-hand sides per thread so
-// every link is read from HBM once per launch however many vectors it is applied to
+// Design: one thread (or TS threads) per output site (grid-stride), NR right-hand sides per
+// thread so every link is read from HBM once per launch however many vectors it is applied to
 // (the multi-RHS form, Sec. 3). Links stream through 16-byte no-L1-allocate loads from
 // their chunk planes; neighbour vectors go through L1/L2, where the 16-fold reuse of
 // each input site is served. Accumulation is FP64 for FP64 storage and FP32 otherwise.
@@ -145,21 +145,32 @@ struct DslashBounds {
   static constexpr int min_blocks = sizeof(LR) == 8 ? 1 : (NR == 1 ? 4 : (NR == 2 ? 1 : (NR == 4 ? 2 : (NR == 8 ? 4 : 1))));
 };
 
-template <typename LR, typename SR, int NR, int EPI, bool COMP = false>
+// TS threads share one output site, each applying its links to NR of the site's NR*TS vectors
+// (thread sub = threadIdx.x % TS takes vectors sub*NR .. sub*NR+NR-1). The TS lanes of a site sit in
+// one warp and load the same link words in the same instruction, so a link still leaves HBM once
+// per launch, while each thread holds fewer accumulators (more warps in flight per SM).
+template <typename LR, typename SR, int NR, int EPI, bool COMP = false, int TS = 1>
 __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR, NR>::min_blocks)
     dslash_kernel(const DslashKArgs k) {
   using A = typename Real<LR>::acc;  // accumulation type follows the link precision
   using SA = typename Real<SR>::acc;
+  static_assert(TS == 1 || TS == 2 || TS == 4, "threads per site");
   if (k.skip && *k.skip) return;  // uniform over the grid
   const Geom& g = k.g;
   const int p = k.out_parity;
   double dot[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) dot[r] = 0.0;
+  const int sub = TS == 1 ? 0 : (int)(threadIdx.x % TS);  // blockDim.x is a multiple of TS
+  const int rbase = sub * NR;
+  const size_t vbytes = (size_t)rbase * k.rhs_stride * 6 * sizeof(SR);
+  const void* in = (const char*)k.in + vbytes;
+  void* out = (char*)k.out + vbytes;
+  const void* y = k.y ? (const void*)((const char*)k.y + vbytes) : nullptr;
 
-  for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.half; cb += gridDim.x * blockDim.x) {
+  for (int cb = (blockIdx.x * blockDim.x + threadIdx.x) / TS; cb < g.half; cb += gridDim.x * blockDim.x / TS) {
     cplx<A> acc[NR][3];
-    dslash_site<LR, SR, NR, COMP>(g, k.links, k.blk_bytes, p, cb, k.in, k.rhs_stride, acc,
+    dslash_site<LR, SR, NR, COMP>(g, k.links, k.blk_bytes, p, cb, in, k.rhs_stride, acc,
                                   Comp12{k.long12, k.blk12, k.inv_naik, k.flags});
 
 #pragma unroll
@@ -171,8 +182,8 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
         for (int i = 0; i < 3; ++i) o[i] = {SA(acc[r][i].re), SA(acc[r][i].im)};
       } else {
         cplx<SA> yv[3];
-        VecIO<SR>::load(k.y, site, yv);
-        const A a = A(k.a[r]);
+        VecIO<SR>::load(y, site, yv);
+        const A a = A(k.a[rbase + r]);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           o[i].re = SA(fma(a, A(yv[i].re), -acc[r][i].re));
@@ -187,7 +198,7 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
           dot[r] += (double)t;
         }
       }
-      VecIO<SR>::store(k.out, site, o);
+      VecIO<SR>::store(out, site, o);
     }
   }
 
@@ -195,14 +206,14 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
     if (k.partials == nullptr) return;  // uniform over the grid
     __shared__ double red[32];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      double s = block_sum_dyn(dot[r], red);
-      if (threadIdx.x == 0) k.partials[(size_t)r * gridDim.x + blockIdx.x] = s;
+    for (int R = 0; R < NR * TS; ++R) {
+      double s = block_sum_dyn(sub == R / NR ? dot[R % NR] : 0.0, red);
+      if (threadIdx.x == 0) k.partials[(size_t)R * gridDim.x + blockIdx.x] = s;
     }
     if (last_block_done(k.counter)) {
-      for (int r = 0; r < NR; ++r) {
-        double s = sum_partials_dyn(k.partials + (size_t)r * gridDim.x, gridDim.x, red);
-        if (threadIdx.x == 0) k.dot_out[r] = s;
+      for (int R = 0; R < NR * TS; ++R) {
+        double s = sum_partials_dyn(k.partials + (size_t)R * gridDim.x, gridDim.x, red);
+        if (threadIdx.x == 0) k.dot_out[R] = s;
       }
     }
   }

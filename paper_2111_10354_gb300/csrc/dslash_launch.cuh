@@ -1,5 +1,5 @@
 // Host-side launcher of the Dslash kernel for one (link, spinor) precision pair: splits
-// nrhs into register-resident groups of NR right-hand sides and picks the block size
+// nrhs into groups that share each link read and picks the launch form and block size
 // with the autotuner.
 #pragma once
 #include <string>
@@ -9,35 +9,62 @@
 
 namespace hisq {
 
-template <typename LR, typename SR, int NR, int EPI, bool COMP>
-static int launch_group(hisq_ctx* ctx, DslashKArgs a, const char* key) {
-  auto kern = dslash_kernel<LR, SR, NR, EPI, COMP>;
-  auto run = [&](int block) -> cudaError_t {
-    int grid = (ctx->g.half + block - 1) / block;
-    // reducing launches: one wave of blocks keeps the partials (and the finishing block's tail) short
-    int cap = (EPI == EPI_AXPY && a.partials) ? ctx->num_sms * (2048 / block) : max_grid_blocks(ctx, block);
-    if (grid > cap) grid = cap;
-    kern<<<grid, block, 0, ctx->stream>>>(a);
-    return cudaGetLastError();
-  };
-  int block = 0;
-  int rc = tuned_block(ctx, key, (const void*)kern, run, &block);
+// One launch form: NR vectors per thread, TS threads per site (NR * TS vectors per launch).
+template <typename LR, typename SR, int NR, int EPI, bool COMP, int TS>
+static TuneVariant dslash_variant(hisq_ctx* ctx, const DslashKArgs& a) {
+  auto kern = dslash_kernel<LR, SR, NR, EPI, COMP, TS>;
+  return TuneVariant{(const void*)kern, [ctx, &a, kern](int block) -> cudaError_t {
+                       int grid = (int)(((size_t)ctx->g.half * TS + block - 1) / block);
+                       // reducing launches: one wave of blocks keeps the partials (and the finishing
+                       // block's tail) short
+                       int cap = (EPI == EPI_AXPY && a.partials) ? ctx->num_sms * (2048 / block)
+                                                                : max_grid_blocks(ctx, block);
+                       if (grid > cap) grid = cap;
+                       kern<<<grid, block, 0, ctx->stream>>>(a);
+                       return cudaGetLastError();
+                     }};
+}
+
+template <int N>
+static int launch_tuned(hisq_ctx* ctx, const char* key, const TuneVariant (&v)[N]) {
+  int vi = 0, block = 0;
+  int rc = tuned_variant(ctx, key, v, N, &vi, &block);
   if (rc != HISQ_OK) return rc;
-  HISQ_CUDA(run(block));
+  HISQ_CUDA(v[vi].run(block));
   note_launch(ctx);
   return HISQ_OK;
 }
 
+// A group of nr vectors shares each link read. The launch forms differ in how the group is spread
+// over threads (vectors per thread x threads per site); the tuner times each and keeps the fastest.
 template <typename LR, typename SR, int EPI, bool COMP>
 static int launch_nr(hisq_ctx* ctx, const DslashKArgs& a, int nr) {
   char key[64];
   snprintf(key, sizeof key, "dslash/l%d/s%d/nr%d/e%d/c%d", Real<LR>::prec, Real<SR>::prec, nr, EPI, (int)COMP);
   switch (nr) {
-    case 1: return launch_group<LR, SR, 1, EPI, COMP>(ctx, a, key);
-    case 2: return launch_group<LR, SR, 2, EPI, COMP>(ctx, a, key);
-    case 4: return launch_group<LR, SR, 4, EPI, COMP>(ctx, a, key);
-    case 8: return launch_group<LR, SR, (sizeof(LR) == 8 ? 4 : 8), EPI, COMP>(ctx, a, key);
-    case 16: return launch_group<LR, SR, (sizeof(LR) == 8 ? 4 : 16), EPI, COMP>(ctx, a, key);
+    case 1: {
+      const TuneVariant v[] = {dslash_variant<LR, SR, 1, EPI, COMP, 1>(ctx, a)};
+      return launch_tuned(ctx, key, v);
+    }
+    case 2: {
+      const TuneVariant v[] = {dslash_variant<LR, SR, 2, EPI, COMP, 1>(ctx, a),
+                               dslash_variant<LR, SR, 1, EPI, COMP, 2>(ctx, a)};
+      return launch_tuned(ctx, key, v);
+    }
+    case 4: {
+      const TuneVariant v[] = {dslash_variant<LR, SR, 4, EPI, COMP, 1>(ctx, a),
+                               dslash_variant<LR, SR, 2, EPI, COMP, 2>(ctx, a),
+                               dslash_variant<LR, SR, 1, EPI, COMP, 4>(ctx, a)};
+      return launch_tuned(ctx, key, v);
+    }
+    case 8:
+      if constexpr (sizeof(LR) < 8) {
+        const TuneVariant v[] = {dslash_variant<LR, SR, 8, EPI, COMP, 1>(ctx, a),
+                                 dslash_variant<LR, SR, 4, EPI, COMP, 2>(ctx, a),
+                                 dslash_variant<LR, SR, 2, EPI, COMP, 4>(ctx, a)};
+        return launch_tuned(ctx, key, v);
+      }
+      break;
   }
   return set_error(HISQ_EINVAL, "unsupported rhs group %d", nr);
 }

@@ -51,12 +51,12 @@ def test_cg_free_field_exact(hisq, inner):
     assert np.linalg.norm(x.cpu().numpy()[0] - x_exact) / np.linalg.norm(x_exact) < 1e-9
 
 
-@pytest.mark.parametrize("inner", [0, 1, 2])
-def test_cg_multi_rhs(hisq, inner):
+@pytest.mark.parametrize("inner,nrhs", [(0, 5), (1, 5), (2, 5), (1, 8), (1, 21), (3, 16)])
+def test_cg_multi_rhs(hisq, inner, nrhs):
+    """Groups of 8 and 16 vectors run with 2 and 4 threads per site; 21 = 16 + 4 + 1."""
     import torch
     L = (8, 10, 12, 14)
     lat, ff, lf = lattice(hisq, L, 7)
-    nrhs = 5
     b = hin.gen_source(70, lat.half, nrhs)
     b[3] *= 1e-3  # different scales per rhs
     x = torch.zeros((nrhs, lat.half, 3), dtype=torch.complex128, device="cuda")

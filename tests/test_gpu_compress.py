@@ -24,7 +24,7 @@ def comp(hisq):
 
 @pytest.mark.parametrize("prec", [1, 2, 3])
 @pytest.mark.parametrize("parity", [0, 1])
-@pytest.mark.parametrize("nrhs", [1, 4])
+@pytest.mark.parametrize("nrhs", [1, 4, 16])
 def test_compressed_dslash_parity(comp, prec, parity, nrhs):
     L, lat, ff, lf = comp
     src = hin.gen_source(100 + nrhs, lat.half, nrhs)

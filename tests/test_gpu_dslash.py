@@ -78,7 +78,7 @@ def test_dslash_parity(hisq, L, prec, parity):
 
 
 @pytest.mark.parametrize("nrhs", [2, 3, 4, 8, 16, 21])
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_dslash_multi_rhs(hisq, nrhs, prec):
     L = (8, 10, 12, 14)
     lat, ff, lf = setup(hisq, L)
