@@ -429,6 +429,9 @@ def run_sweep():
                                   "frac_hbm": round(by / ms / 1e6 / peak, 3),
                                   "sites_per_s": round(nrhs * V / 2 / (ms * 1e-3), 1),
                                   "GFLOP/s": round(1146 * nrhs * V / 2 / (ms * 1e-3) / 1e9, 1)}), flush=True)
+        # the tuner's choice per kernel: variant * 10000 + block (1-vector forms: variant 1 = z-slowest walk)
+        print(json.dumps({"lattice": "x".join(map(str, L)), "tuned": h.hisq_tune_report(lat.ctx).splitlines()}),
+              flush=True)
         lat.close()
         del lat
         torch.cuda.empty_cache()

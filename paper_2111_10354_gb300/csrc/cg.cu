@@ -132,25 +132,64 @@ __global__ void k_reliable(const double2* __restrict__ r_hi, S* __restrict__ r_l
   }
 }
 
-// Complex vector access per site (3 colours) for the BLAS kernels.
-template <typename S>
-struct Site3 {
-  using T = typename Real<S>::acc;
-  __device__ __forceinline__ static void load(const S* v, size_t site, cplx<T> o[3]) { VecIO<S>::load(v, site, o); }
-  __device__ __forceinline__ static void store(S* v, size_t site, const cplx<T> o[3]) { VecIO<S>::store(v, site, o); }
-};
 
-// One CG update per site: x += alpha*p (X = double: the FP64 solution itself, plain CG; X = float:
+// Flat 16-byte access to vectors of complex entries for the BLAS kernels: the updates are
+// entry-wise, so a thread takes Chunk<S>::K consecutive complex entries (one 16-byte load per
+// vector; FP32 2, FP64 1) regardless of site boundaries. A rhs holds 3 * half complex
+// entries, a multiple of 24, so chunks never straddle two rhs.
+template <typename S>
+struct Chunk;
+template <>
+struct Chunk<float> {
+  static constexpr int K = 2;
+  __device__ __forceinline__ static void load(const float* v, size_t c, cplx<float> o[2]) {
+    const float4 w = reinterpret_cast<const float4*>(v)[c];
+    o[0] = {w.x, w.y};
+    o[1] = {w.z, w.w};
+  }
+  __device__ __forceinline__ static void store(float* v, size_t c, const cplx<float> o[2]) {
+    reinterpret_cast<float4*>(v)[c] = make_float4(o[0].re, o[0].im, o[1].re, o[1].im);
+  }
+};
+template <>
+struct Chunk<double> {
+  static constexpr int K = 1;
+  __device__ __forceinline__ static void load(const double* v, size_t c, cplx<double> o[1]) {
+    const double2 w = reinterpret_cast<const double2*>(v)[c];
+    o[0] = {w.x, w.y};
+  }
+  __device__ __forceinline__ static void store(double* v, size_t c, const cplx<double> o[1]) {
+    reinterpret_cast<double2*>(v)[c] = make_double2(o[0].re, o[0].im);
+  }
+};
+// K complex entries starting at entry index e (a multiple of K), in as many chunks of X as needed.
+template <typename X, int K>
+__device__ __forceinline__ void load_k(const X* v, size_t e, cplx<typename Real<X>::acc> o[K]) {
+  constexpr int KX = Chunk<X>::K;
+  static_assert(K % KX == 0, "chunk sizes");
+#pragma unroll
+  for (int j = 0; j < K / KX; ++j) Chunk<X>::load(v, e / KX + j, o + j * KX);
+}
+template <typename X, int K>
+__device__ __forceinline__ void store_k(X* v, size_t e, const cplx<typename Real<X>::acc> o[K]) {
+  constexpr int KX = Chunk<X>::K;
+#pragma unroll
+  for (int j = 0; j < K / KX; ++j) Chunk<X>::store(v, e / KX + j, o + j * KX);
+}
+
+// One CG update, entry-wise: x += alpha*p (X = double: the FP64 solution itself, plain CG; X = float:
 // the FP32 correction e of the current reliable cycle, mixed precision); r -= alpha*Ap;
-// rr_new = |r|^2 with the site's term in the arithmetic precision, summed over sites in FP64.
+// rr_new = |r|^2 with each chunk's term in the arithmetic precision, summed over chunks in FP64.
+// n: complex entries per rhs (3 * half).
 template <typename S, typename X>
-__global__ void k_update(X* __restrict__ x, S* __restrict__ r, const S* __restrict__ p, const S* __restrict__ Ap,
-                         size_t nsite, SolverState* st, double* partials, size_t pstride, unsigned* counter) {
+__global__ void __launch_bounds__(256, 6) k_update(X* __restrict__ x, S* __restrict__ r, const S* __restrict__ p, const S* __restrict__ Ap,
+                         size_t n, SolverState* st, double* partials, size_t pstride, unsigned* counter) {
   if (st->done) return;
   using T = typename Real<S>::acc;
   using XT = typename Real<X>::acc;
+  constexpr int K = Chunk<S>::K;
   const int rh = blockIdx.y;
-  const size_t off = (size_t)rh * nsite;
+  const size_t off = (size_t)rh * n;
   double v[1] = {0.0};
   const double pap = st->pAp[rh];
   const bool active = !st->rhs_done[rh] && pap > 0.0 && isfinite(pap);
@@ -159,28 +198,28 @@ __global__ void k_update(X* __restrict__ x, S* __restrict__ r, const S* __restri
   // X = double: x is the solution itself, in true units (alpha * scale); X = float: e is in
   // inner units and k_fold applies the scale
   const XT ax = XT(sizeof(X) == 8 ? alpha * st->scale[rh] : alpha);
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nsite; i += (size_t)gridDim.x * blockDim.x) {
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < n; i += (size_t)gridDim.x * blockDim.x * K) {
     if (st->rhs_done[rh]) break;  // frozen rhs: its vectors are not touched (uniform per block)
-    cplx<T> pv[3], rv[3], av[3];
-    Site3<S>::load(p, off + i, pv);
-    Site3<S>::load(r, off + i, rv);
+    cplx<T> pv[K], rv[K], av[K];
+    Chunk<S>::load(p, (off + i) / K, pv);
+    Chunk<S>::load(r, (off + i) / K, rv);
     if (active) {
-      cplx<XT> xv[3];
-      Site3<X>::load(x, off + i, xv);
-      Site3<S>::load(Ap, off + i, av);
+      cplx<XT> xv[K];
+      load_k<X, K>(x, off + i, xv);
+      Chunk<S>::load(Ap, (off + i) / K, av);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < K; ++c) {
         xv[c].re = fma(ax, XT(pv[c].re), xv[c].re);
         xv[c].im = fma(ax, XT(pv[c].im), xv[c].im);
         rv[c].re = fma(-a, av[c].re, rv[c].re);
         rv[c].im = fma(-a, av[c].im, rv[c].im);
       }
-      Site3<X>::store(x, off + i, xv);
-      Site3<S>::store(r, off + i, rv);
+      store_k<X, K>(x, off + i, xv);
+      Chunk<S>::store(r, (off + i) / K, rv);
     }
     T t = T(0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) t += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
+    for (int c = 0; c < K; ++c) t += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
     v[0] += (double)t;
   }
   double out[1][MAXR];
@@ -194,27 +233,29 @@ __global__ void k_update(X* __restrict__ x, S* __restrict__ r, const S* __restri
   }
 }
 
-// p = r + beta*p with beta = rr_new / rr; then (last block) commit rr, iteration counts,
-// per-rhs inner convergence and the end-of-cycle flag.
+// p = r + beta*p with beta = rr_new / rr, entry-wise; then (last block) commit rr, iteration
+// counts, per-rhs inner convergence and the end-of-cycle flag. n: complex entries per rhs.
 template <typename S>
-__global__ void k_pupdate(const S* __restrict__ r, S* __restrict__ p, size_t nsite, SolverState* st,
+__global__ void __launch_bounds__(256, 8) k_pupdate(const S* __restrict__ r, S* __restrict__ p, size_t n, SolverState* st,
                           unsigned* counter) {
   if (st->done) return;
   using T = typename Real<S>::acc;
+  constexpr int K = Chunk<S>::K;
   const int rh = blockIdx.y;
-  const size_t off = (size_t)rh * nsite;
+  const size_t off = (size_t)rh * n;
   if (!st->rhs_done[rh]) {
     const T beta = T(st->rr_new[rh] / st->rr[rh]);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nsite; i += (size_t)gridDim.x * blockDim.x) {
-      cplx<T> pv[3], rv[3];
-      Site3<S>::load(p, off + i, pv);
-      Site3<S>::load(r, off + i, rv);
+    for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < n;
+         i += (size_t)gridDim.x * blockDim.x * K) {
+      cplx<T> pv[K], rv[K];
+      Chunk<S>::load(p, (off + i) / K, pv);
+      Chunk<S>::load(r, (off + i) / K, rv);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < K; ++c) {
         pv[c].re = fma(beta, pv[c].re, rv[c].re);
         pv[c].im = fma(beta, pv[c].im, rv[c].im);
       }
-      Site3<S>::store(p, off + i, pv);
+      Chunk<S>::store(p, (off + i) / K, pv);
     }
   }
   if (last_block_done(counter) && threadIdx.x == 0) {
@@ -266,9 +307,9 @@ struct CgBuffers {
   double* partials;
 };
 
-static dim3 blas_grid(const hisq_ctx* ctx, int nrhs, size_t units) {
+static dim3 blas_grid(const hisq_ctx* ctx, int nrhs, size_t units, int per_sm = 8) {
   size_t gx = (units + 255) / 256;
-  const size_t cap = (size_t)ctx->num_sms * 8;  // one wave of 256-thread blocks (grid-stride beyond)
+  const size_t cap = (size_t)ctx->num_sms * per_sm;  // one wave of 256-thread blocks (grid-stride beyond)
   if (gx > cap) gx = cap;
   if (gx < 1) gx = 1;
   return dim3((unsigned)gx, nrhs);
@@ -337,15 +378,16 @@ static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
   c2.dot_out = B.st->pAp;
   c2.counter = ctx->d_counters + 3;
   if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
-  dim3 grid = blas_grid(ctx, nrhs);
-  const size_t nsite = ctx->g.half;
-  if (sizeof(S) == 8)
-    k_update<S, double><<<grid, 256, 0, ctx->stream>>>((double*)B.x, (S*)B.r, (const S*)B.p, (const S*)B.Ap, nsite,
+  // one thread per 16-byte chunk of each vector, one wave of resident blocks (6 or 8 per SM)
+  dim3 grid = blas_grid(ctx, nrhs, n / Chunk<S>::K, 6);
+  if constexpr (sizeof(S) == 8)
+    k_update<S, double><<<grid, 256, 0, ctx->stream>>>((double*)B.x, (S*)B.r, (const S*)B.p, (const S*)B.Ap, n,
                                                        B.st, B.partials, partial_stride(ctx), ctx->d_counters + 4);
   else
-    k_update<S, float><<<grid, 256, 0, ctx->stream>>>((float*)B.e, (S*)B.r, (const S*)B.p, (const S*)B.Ap, nsite,
+    k_update<S, float><<<grid, 256, 0, ctx->stream>>>((float*)B.e, (S*)B.r, (const S*)B.p, (const S*)B.Ap, n,
                                                       B.st, B.partials, partial_stride(ctx), ctx->d_counters + 4);
-  k_pupdate<S><<<grid, 256, 0, ctx->stream>>>((const S*)B.r, (S*)B.p, nsite, B.st, ctx->d_counters + 5);
+  k_pupdate<S><<<blas_grid(ctx, nrhs, n / Chunk<S>::K, 8), 256, 0, ctx->stream>>>((const S*)B.r, (S*)B.p, n, B.st,
+                                                                               ctx->d_counters + 5);
   HISQ_CUDA(cudaGetLastError());
   note_launch(ctx, 2);
   return HISQ_OK;
@@ -585,16 +627,24 @@ __global__ void k_ms_rupdate(S* __restrict__ r, const S* __restrict__ Ap, size_t
                              size_t pstride, unsigned* counter) {
   if (st->done) return;
   using T = typename Real<S>::acc;
+  constexpr int K = Chunk<S>::K;
   const double pap = st->pAp;
   const double alpha = (pap > 0.0 && isfinite(pap)) ? st->rr / pap : 0.0;
   const T a = T(alpha);
   double v = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    T re = fma(-a, T(Ap[2 * i]), T(r[2 * i]));
-    T im = fma(-a, T(Ap[2 * i + 1]), T(r[2 * i + 1]));
-    r[2 * i] = S(re);
-    r[2 * i + 1] = S(im);
-    v += (double)re * (double)re + (double)im * (double)im;
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < n; i += (size_t)gridDim.x * blockDim.x * K) {
+    cplx<T> rv[K], av[K];
+    Chunk<S>::load(r, i / K, rv);
+    Chunk<S>::load(Ap, i / K, av);
+    T t = T(0);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      rv[c].re = fma(-a, av[c].re, rv[c].re);
+      rv[c].im = fma(-a, av[c].im, rv[c].im);
+      t += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
+    }
+    Chunk<S>::store(r, i / K, rv);
+    v += (double)t;
   }
   __shared__ double red[32];
   double s = block_sum_dyn(v, red);
@@ -643,18 +693,26 @@ __global__ void k_ms_update(double2* __restrict__ x, S* __restrict__ p, const S*
     s_b[k] = T(st->beta_k[k]);
   }
   __syncthreads();
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const T rre = T(r[2 * i]), rim = T(r[2 * i + 1]);
+  constexpr int K = Chunk<S>::K;
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < n; i += (size_t)gridDim.x * blockDim.x * K) {
+    cplx<T> rv[K];
+    Chunk<S>::load(r, i / K, rv);
     for (int k = 0; k < ns; ++k) {
       if (!s_act[k]) continue;
       const size_t j = (size_t)k * n + i;
-      const T pre = T(p[2 * j]), pim = T(p[2 * j + 1]);
-      double2 xv = x[j];
-      xv.x += s_ax[k] * (double)pre;
-      xv.y += s_ax[k] * (double)pim;
-      x[j] = xv;
-      p[2 * j] = S(fma(s_b[k], pre, s_z[k] * rre));
-      p[2 * j + 1] = S(fma(s_b[k], pim, s_z[k] * rim));
+      cplx<T> pv[K];
+      cplx<double> xv[K];
+      Chunk<S>::load(p, j / K, pv);
+      load_k<double, K>((const double*)x, j, xv);
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        xv[c].re += s_ax[k] * (double)pv[c].re;
+        xv[c].im += s_ax[k] * (double)pv[c].im;
+        pv[c].re = fma(s_b[k], pv[c].re, s_z[k] * rv[c].re);
+        pv[c].im = fma(s_b[k], pv[c].im, s_z[k] * rv[c].im);
+      }
+      store_k<double, K>((double*)x, j, xv);
+      Chunk<S>::store(p, j / K, pv);
     }
   }
   if (!last_block_done(counter) || threadIdx.x != 0) return;
@@ -744,7 +802,7 @@ static int ms_iteration(hisq_ctx* ctx, int lp, double2* x, S* r, S* p, S* Ap, S*
   c2.dot_out = &st->pAp;
   c2.counter = ctx->d_counters + 6;
   if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
-  const int grid = blas_grid(ctx, 1).x;
+  const int grid = blas_grid(ctx, 1, n / Chunk<S>::K, 4).x;  // one thread per 16-byte chunk, one wave
   k_ms_rupdate<S><<<grid, 256, 0, ctx->stream>>>(r, Ap, n, st, partials, partial_stride(ctx), ctx->d_counters + 7);
   k_ms_update<S><<<grid, 256, 0, ctx->stream>>>(x, p, r, n, st, ctx->d_counters + 8);
   HISQ_CUDA(cudaGetLastError());
