@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the steps only: no e2e, comparison solves or CPU baseline (for profiler launch lists)")
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
-    ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8", "ptc", "batch"],
+    ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-df64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8",
+                                                   "ptc", "batch"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
@@ -217,7 +218,7 @@ def aggregate(t_local, bytes_local, dist, device):
 def vec_like(torch, half, prec, nrhs=1, seed=5):
     import hisq_inputs as hin
     v = torch.from_numpy(hin.gen_source(seed, half, nrhs))
-    if prec == 0:
+    if prec in (0, 4):  # FP64 and double-float take complex128 vectors
         return v.cuda()
     if prec == 1:
         return v.to(torch.complex64).cuda()
@@ -264,7 +265,7 @@ def run_ours(args, rank, world, local):
 
     fat, lng, b_np = gen_workload(rank)
     stream = torch.cuda.Stream()
-    lat = h.Lattice(DIMS, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16), stream=stream).load(fat, lng)
+    lat = h.Lattice(DIMS, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16, h.HISQ_DF64), stream=stream).load(fat, lng)
     half = lat.half
     b = torch.from_numpy(b_np).cuda()
     x = torch.zeros_like(b)
@@ -331,12 +332,15 @@ def run_ours(args, rank, world, local):
     achieved = bytes_launch / (ms_launch * 1e-3) / 1e9
     launches += 2 * (reps + 3)
 
-    # time-to-1e-10 comparisons (mixed FP32, mixed FP16, plain FP64) at both masses
+    # time-to-1e-10 comparisons (mixed FP32, mixed FP16, plain FP64) at both masses, and the same with the
+    # double-float operator (plain CG, and FP32 inner with double-float reliable updates); every solve is
+    # judged by its true residual
     cmp = {}
     for m in (0.01, 0.002):
         row = {}
         for name, o in (("mixed_f32", dict(inner_prec=h.HISQ_F32)), ("mixed_f16", dict(inner_prec=h.HISQ_F16)),
-                        ("fp64", dict(inner_prec=h.HISQ_F64))):
+                        ("fp64", dict(inner_prec=h.HISQ_F64)), ("df64", dict(inner_prec=h.HISQ_DF64)),
+                        ("mixed_f32_df64_reliable", dict(inner_prec=h.HISQ_F32, reliable_prec=h.HISQ_DF64))):
             xs = torch.zeros_like(b)
             lat.cg(xs, b, m, TOL, 20000, **o)  # first call tunes this variant's kernels
             xs.zero_()
@@ -377,8 +381,8 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 reliable", "data": "synthetic",
         "config": {"workload": workload_name(), "lattice": list(DIMS), "mass": MASS, "tol": TOL,
                    "inner_prec": "f32", "reliable_period": 50, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2: FP64+FP32+FP16 links %.2f GB resident" % (
-                       half * 16 * 18 * (8 + 4 + 2) / 1e9),
+                   "l2": "inputs larger than L2: FP64+FP32+FP16+double-float links %.2f GB resident" % (
+                       half * 16 * 18 * (8 + 4 + 2 + 8) / 1e9),
                    "iters_per_solve": iters[0][0], "reliable_updates": iters[0][1],
                    "worst_true_rel_residual": worst_res},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -412,7 +416,9 @@ def run_sweep():
     sizes = [(32, 32, 32, 8), (48, 48, 48, 12), (64, 64, 64, 16), (96, 96, 96, 24), (144, 144, 144, 36)]
     for L in sizes:
         V = int(np.prod(L))
-        precs = (h.HISQ_F64, h.HISQ_F32, h.HISQ_F16)
+        # double-float links are resident too where they fit beside the others (not at 144^3x36, where
+        # FP64 + FP32 + FP16 already take 217 GB)
+        precs = (h.HISQ_F64, h.HISQ_F32, h.HISQ_F16) + ((h.HISQ_DF64,) if L[0] < 144 else ())
         lat = h.Lattice(L, precs=precs, stream=stream)
         # slab by slab keeps the host link arrays small even at 144^3x36
         nt = max(1, min(L[3], int(2e8 // (L[0] * L[1] * L[2] * 4 * 9 * 16))))
@@ -631,11 +637,13 @@ def run_kernel_case(name):
     if name.startswith("dslash"):
         L = (48, 48, 48, 12)
         fat, lng = hin.gen_links(L, 1001, 0.3, 0.1)
-        lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16), stream=stream)
+        lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16) + ((h.HISQ_DF64,) if name == "dslash-df64" else ()),
+                        stream=stream)
         if name == "dslash-f32-comp":
             lat.compress_long(-1.0 / 24.0)
         lat.load(fat, lng)
-        prec = {"dslash-f64": h.HISQ_F64, "dslash-f16": h.HISQ_F16, "dslash-f32-comp": h.HISQ_F32,
+        prec = {"dslash-f64": h.HISQ_F64, "dslash-df64": h.HISQ_DF64, "dslash-f16": h.HISQ_F16,
+                "dslash-f32-comp": h.HISQ_F32,
                 "dslash-f32-nr8": h.HISQ_F32}[name]
         ms = time_dslash(torch, lat, prec, 8 if name.endswith("nr8") else 1, 4, stream)
         print(json.dumps({"case": name, "us": round(ms * 1e3, 2)}))

@@ -25,8 +25,9 @@
  *   links      host, complex128 interleaved (re, im), [t][z][y][x][mu][row][col],
  *              x fastest, mu = 0..3 = x, y, z, t.
  *   vectors    [rhs][cb][color] over the sites of one parity, complex numbers stored
- *              as (re, im) pairs of the precision's real type: HISQ_F64 complex128,
- *              HISQ_F32 complex64, HISQ_F16 two IEEE binary16, HISQ_BF16 two bfloat16.
+ *              as (re, im) pairs of the precision's real type: HISQ_F64 and HISQ_DF64
+ *              complex128, HISQ_F32 complex64, HISQ_F16 two IEEE binary16, HISQ_BF16 two
+ *              bfloat16.
  *              Solver vectors are always complex128. A vector argument may point to
  *              device memory or to host memory (pageable or pinned); host data is
  *              staged through library-owned device buffers on the context's stream.
@@ -66,9 +67,19 @@ enum {
 };
 
 /* ---------------------------------------------------------------- precisions */
-typedef enum { HISQ_F64 = 0, HISQ_F32 = 1, HISQ_F16 = 2, HISQ_BF16 = 3 } hisq_prec;
+/*
+ * HISQ_DF64 ("double-float") is an FP64-class precision that runs on the FP32 pipe: vectors
+ * at the boundary are complex128 as for HISQ_F64, links are stored as pairs of FP32 words
+ * (hi + lo, 16 bytes per complex entry like FP64) and the Dslash arithmetic is double-float
+ * (error-free FP32 transformations, 2^-47 relative rounding per operation against FP64's
+ * 2^-53). It exists because GB300 executes FP64 at ~1/60 of its FP32 rate, which makes the
+ * FP64 Dslash arithmetic-bound; the double-float one is bandwidth-bound. Vector entries must
+ * have magnitude below 2^127; entries below 2^-100 are treated as zero. The paper has no
+ * counterpart. Not available for 16-bit link compression or the batched solver.
+ */
+typedef enum { HISQ_F64 = 0, HISQ_F32 = 1, HISQ_F16 = 2, HISQ_BF16 = 3, HISQ_DF64 = 4 } hisq_prec;
 #define HISQ_PREC_BIT(p) (1u << (unsigned)(p))
-#define HISQ_PREC_ALL 0xFu
+#define HISQ_PREC_ALL 0x1Fu
 
 /* ---------------------------------------------------------------- link-load flags */
 #define HISQ_APPLY_PHASES 1u   /* multiply eta_mu(x) into fat and long links */
@@ -123,7 +134,8 @@ int hisq_set_long_compression(hisq_ctx* ctx, double naik);
  * out = D_eo in (out_parity = 0: out on even sites, in on odd sites), or
  * out = D_oe in (out_parity = 1). Vectors in precision prec (its links must be
  * resident), nrhs vectors of V/2 sites back to back; out and in must not overlap.
- * Arithmetic: FP64 for HISQ_F64, FP32 for the others (16-bit types are storage only).
+ * Arithmetic: FP64 for HISQ_F64, double-float for HISQ_DF64, FP32 for the others (16-bit
+ * types are storage only).
  * Asynchronous on the context's stream for device pointers.
  * Errors: HISQ_EINVAL (parity, nrhs < 1 or > 64, precision not resident), HISQ_ENOLINKS.
  */
@@ -137,12 +149,16 @@ int hisq_apply_A(hisq_ctx* ctx, void* out, const void* in, double mass, double s
 
 /* ---------------------------------------------------------------- solvers */
 typedef struct {
-  int inner_prec;       /* HISQ_F64: plain FP64 CG. HISQ_F32 / F16 / BF16: mixed precision --
-                           inner CG with links in that precision, FP32 spinors and arithmetic,
-                           FP64 reductions and FP64 solution accumulator, FP64 reliable updates */
-  int reliable_period;  /* inner iterations between FP64 reliable updates (default 50) */
+  int inner_prec;       /* HISQ_F64: plain FP64 CG. HISQ_DF64: plain CG with the double-float
+                           operator (FP64 vectors and BLAS). HISQ_F32 / F16 / BF16: mixed
+                           precision -- inner CG with links in that precision, FP32 spinors and
+                           arithmetic, FP64 reductions and FP64 solution accumulator, reliable
+                           updates in reliable_prec */
+  int reliable_period;  /* inner iterations between reliable updates (default 50) */
   int use_graph;        /* 1: capture blocks of iterations in a CUDA graph (default 1) */
   int poll_every;       /* iterations between host convergence polls (default 25) */
+  int reliable_prec;    /* operator precision of reliable updates and true residuals:
+                           HISQ_F64 (default) or HISQ_DF64 (its links must be resident) */
 } hisq_solver_opts;
 
 typedef struct {

@@ -27,11 +27,11 @@ HISQ_ENOCONV = -6
 HISQ_EBREAKDOWN = -7
 HISQ_ETIMEOUT = -8
 
-HISQ_F64, HISQ_F32, HISQ_F16, HISQ_BF16 = 0, 1, 2, 3
-PREC_NAMES = {HISQ_F64: "f64", HISQ_F32: "f32", HISQ_F16: "f16", HISQ_BF16: "bf16"}
+HISQ_F64, HISQ_F32, HISQ_F16, HISQ_BF16, HISQ_DF64 = 0, 1, 2, 3, 4
+PREC_NAMES = {HISQ_F64: "f64", HISQ_F32: "f32", HISQ_F16: "f16", HISQ_BF16: "bf16", HISQ_DF64: "df64"}
 HISQ_APPLY_PHASES = 1
 HISQ_ANTIPERIODIC_T = 2
-HISQ_PREC_ALL = 0xF
+HISQ_PREC_ALL = 0x1F
 HISQ_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -41,7 +41,7 @@ def HISQ_PREC_BIT(p: int) -> int:
 
 class hisq_solver_opts(ctypes.Structure):
     _fields_ = [("inner_prec", ctypes.c_int), ("reliable_period", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("poll_every", ctypes.c_int)]
+                ("poll_every", ctypes.c_int), ("reliable_prec", ctypes.c_int)]
 
 
 class hisq_solver_stats(ctypes.Structure):
@@ -212,10 +212,12 @@ def hisq_solver_opts_default() -> hisq_solver_opts:
     return o
 
 
-def make_opts(inner_prec: int = HISQ_F64, reliable_period: int = 50, use_graph: bool = True, poll_every: int = 25):
+def make_opts(inner_prec: int = HISQ_F64, reliable_period: int = 50, use_graph: bool = True, poll_every: int = 25,
+              reliable_prec: int = HISQ_F64):
     o = hisq_solver_opts_default()
     o.inner_prec, o.reliable_period, o.use_graph, o.poll_every = inner_prec, reliable_period, int(use_graph), \
         poll_every
+    o.reliable_prec = reliable_prec
     return o
 
 

@@ -14,6 +14,7 @@ int dslash_launch_f64(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_f32(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_f16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_bf16(hisq_ctx* ctx, int sp, const DslashCall& c);
+int dslash_launch_df64(hisq_ctx* ctx, int sp, const DslashCall& c);
 
 static thread_local char g_last_error[512] = "";
 
@@ -55,6 +56,7 @@ int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
     case HISQ_F32: return dslash_launch_f32(ctx, sp, c);
     case HISQ_F16: return dslash_launch_f16(ctx, sp, c);
     case HISQ_BF16: return dslash_launch_bf16(ctx, sp, c);
+    case HISQ_DF64: return dslash_launch_df64(ctx, sp, c);
   }
   return set_error(HISQ_EINVAL, "bad precision %d", lp);
 }
@@ -69,8 +71,8 @@ double dslash_bytes(const hisq_ctx* ctx, int lp, int sp, int nrhs) {
 // antiperiodic-t sign (fat at t = Lt-1, long at t >= Lt-3), then store the link in the
 // chunk-plane layout of every resident precision. Non-finite entries raise *bad.
 __global__ void pack_links_kernel(Geom g, const double2* __restrict__ fat, const double2* __restrict__ lng, int t0,
-                                  int nt, unsigned flags, char* l64, char* l32, char* l16, char* lbf, int* bad,
-                                  double naik, char* c32, char* c16, char* cbf) {
+                                  int nt, unsigned flags, char* l64, char* l32, char* l16, char* lbf, char* ldf,
+                                  int* bad, double naik, char* c32, char* c16, char* cbf) {
   const int slab = g.L[0] * g.L[1] * g.L[2];
   const int n = slab * nt;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -142,6 +144,7 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ fat, const
         if (l32) LinkIO<float>::store(l32 + blk * link_block_bytes(HISQ_F32, g.half), g.half, cb, U);
         if (l16) LinkIO<__half>::store(l16 + blk * link_block_bytes(HISQ_F16, g.half), g.half, cb, U);
         if (lbf) LinkIO<__nv_bfloat16>::store(lbf + blk * link_block_bytes(HISQ_BF16, g.half), g.half, cb, U);
+        if (ldf) LinkIO<df64>::store(ldf + blk * link_block_bytes(HISQ_DF64, g.half), g.half, cb, U);
       }
     }
   }
@@ -154,7 +157,7 @@ int pack_links_slab(hisq_ctx* ctx, const double* d_fat, const double* d_long, in
   if (grid > ctx->num_sms * 32) grid = ctx->num_sms * 32;
   pack_links_kernel<<<grid, block, 0, ctx->stream>>>(ctx->g, (const double2*)d_fat, (const double2*)d_long, t0, nt,
                                                      flags, ctx->links[0], ctx->links[1], ctx->links[2],
-                                                     ctx->links[3], ctx->d_flag, ctx->naik, ctx->long12[1],
+                                                     ctx->links[3], ctx->links[4], ctx->d_flag, ctx->naik, ctx->long12[1],
                                                      ctx->long12[2], ctx->long12[3]);
   HISQ_CUDA(cudaGetLastError());
   note_launch(ctx);
@@ -236,7 +239,7 @@ int hisq_create(hisq_ctx** out, const int dims[4], unsigned prec_mask, void* str
     c->own_stream = true;
   }
   int rc = HISQ_OK;
-  for (int p = 0; p < 4 && rc == HISQ_OK; ++p) {
+  for (int p = 0; p < NPREC && rc == HISQ_OK; ++p) {
     if (!(c->prec_mask & HISQ_PREC_BIT(p))) continue;
     size_t bytes = 16 * link_block_bytes(p, c->g.half);
     e = cudaMalloc((void**)&c->links[p], bytes);
@@ -261,7 +264,7 @@ int hisq_create(hisq_ctx** out, const int dims[4], unsigned prec_mask, void* str
 int hisq_destroy(hisq_ctx* c) {
   if (!c) return HISQ_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < NPREC; ++p) {
     cudaFree(c->links[p]);
     cudaFree(c->long12[p]);
   }
@@ -327,7 +330,7 @@ int hisq_load_links(hisq_ctx* c, const double* fat, const double* lng, unsigned 
 
 static int check_vec_args(hisq_ctx* c, int prec, int nrhs) {
   if (!c) return set_error(HISQ_EINVAL, "null context");
-  if (prec < 0 || prec > 3) return set_error(HISQ_EINVAL, "bad precision %d", prec);
+  if (prec < 0 || prec >= NPREC) return set_error(HISQ_EINVAL, "bad precision %d", prec);
   if (!c->links[prec]) return set_error(HISQ_EINVAL, "precision %d not resident", prec);
   if (nrhs < 1 || nrhs > 64) return set_error(HISQ_EINVAL, "nrhs %d outside [1, 64]", nrhs);
   if (!c->links_ready) return set_error(HISQ_ENOLINKS, "links not loaded");
@@ -339,7 +342,7 @@ static size_t vec_bytes(const hisq_ctx* c, int prec, int nrhs) {
 }
 
 static bool aligned(const void* p, int prec) {
-  size_t a = prec == HISQ_F64 ? 16 : prec == HISQ_F32 ? 8 : 4;
+  size_t a = (prec == HISQ_F64 || prec == HISQ_DF64) ? 16 : prec == HISQ_F32 ? 8 : 4;
   return ((uintptr_t)p % a) == 0;
 }
 
@@ -444,7 +447,7 @@ int hisq_set_long_compression(hisq_ctx* c, double naik) {
 }
 
 double hisq_dslash_bytes(const hisq_ctx* c, int prec, int nrhs) {
-  if (!c || prec < 0 || prec > 3) return 0.0;
+  if (!c || prec < 0 || prec >= NPREC) return 0.0;
   return dslash_bytes(c, prec, prec, nrhs);
 }
 

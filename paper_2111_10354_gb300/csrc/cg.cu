@@ -305,6 +305,7 @@ struct CgBuffers {
   void* e;               // mixed precision: FP32 correction of the current cycle (else == x)
   SolverState* st;
   double* partials;
+  int rp = HISQ_F64;     // operator precision of the true residual: HISQ_F64 or HISQ_DF64
 };
 
 static dim3 blas_grid(const hisq_ctx* ctx, int nrhs, size_t units, int per_sm = 8) {
@@ -316,7 +317,7 @@ static dim3 blas_grid(const hisq_ctx* ctx, int nrhs, size_t units, int per_sm = 
 }
 static dim3 blas_grid(const hisq_ctx* ctx, int nrhs) { return blas_grid(ctx, nrhs, (size_t)ctx->g.half); }
 
-// r_hi = b - A_64 x; rr_true (and bb with init).
+// r_hi = b - A x with the reliable-update operator (FP64, or double-float); rr_true (and bb with init).
 static int true_residual(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int init) {
   const size_t n = (size_t)ctx->g.half * 3;
   DslashCall c1;
@@ -325,7 +326,7 @@ static int true_residual(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int init) 
   c1.in = B.x;
   c1.nrhs = nrhs;
   c1.rhs_stride = ctx->g.half;
-  int rc = dslash_launch(ctx, HISQ_F64, HISQ_F64, c1);
+  int rc = dslash_launch(ctx, B.rp, HISQ_F64, c1);
   if (rc != HISQ_OK) return rc;
   DslashCall c2 = c1;
   c2.out_parity = 0;
@@ -334,7 +335,7 @@ static int true_residual(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int init) 
   c2.y = B.x;
   c2.a_rhs = B.a.data();
   c2.epi = EPI_AXPY;
-  if ((rc = dslash_launch(ctx, HISQ_F64, HISQ_F64, c2)) != HISQ_OK) return rc;
+  if ((rc = dslash_launch(ctx, B.rp, HISQ_F64, c2)) != HISQ_OK) return rc;
   k_residual<<<blas_grid(ctx, nrhs), 256, 0, ctx->stream>>>(B.b, B.b_stride, B.Ax, B.r_hi, n, B.st, B.partials,
                                                             partial_stride(ctx), ctx->d_counters + 1, init);
   HISQ_CUDA(cudaGetLastError());
@@ -402,12 +403,13 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
                   hisq_solver_stats* stats) {
   auto t_start = std::chrono::steady_clock::now();
   const int lp = o.inner_prec;
-  const bool mixed = lp != HISQ_F64;
+  const bool mixed = sizeof(S) == 4;  // FP32 inner vectors (FP64 and double-float CG are plain)
   const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
   const size_t n = (size_t)ctx->g.half * 3;
   const size_t vb64 = (size_t)nrhs * n * sizeof(double2);
   const size_t vbS = (size_t)nrhs * n * 2 * sizeof(S);
   CgBuffers B;
+  B.rp = o.reliable_prec;
   B.x = x;
   B.b = const_cast<double2*>(b);
   B.b_stride = b_stride;
@@ -461,7 +463,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   } else {
     if ((rc = true_residual(ctx, B, nrhs, 1)) != HISQ_OK) return rc;
     dcalls += 2;
-    dbytes += 2 * dslash_bytes(ctx, HISQ_F64, HISQ_F64, nrhs);
+    dbytes += 2 * dslash_bytes(ctx, B.rp, HISQ_F64, nrhs);
   }
   HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
   HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -566,7 +568,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
       if ((rc = true_residual(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
       if ((rc = reliable<S>(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
       dcalls += 2;
-      dbytes += 2 * dslash_bytes(ctx, HISQ_F64, HISQ_F64, nrhs);
+      dbytes += 2 * dslash_bytes(ctx, B.rp, HISQ_F64, nrhs);
       ++reliable_updates;
       verified = true;
       HISQ_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
@@ -943,7 +945,7 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
   // Verification in FP64 and, where a shift's true residual misses its tolerance, refinement:
   // one multi-rhs CG over all shifts (per-rhs shift sigma_k, same source), so every link read
   // serves all shifts. Inner precision as requested.
-  if (lp == HISQ_F64) return run_cg<double>(ctx, x, b, 0, ns, mass, shifts, tol, remaining, o, stats);
+  if (lp == HISQ_F64 || lp == HISQ_DF64) return run_cg<double>(ctx, x, b, 0, ns, mass, shifts, tol, remaining, o, stats);
   return run_cg<float>(ctx, x, b, 0, ns, mass, shifts, tol, remaining, o, stats);
 }
 
@@ -975,6 +977,7 @@ void hisq_solver_opts_default(hisq_solver_opts* o) {
   o->reliable_period = 50;
   o->use_graph = 1;
   o->poll_every = 25;
+  o->reliable_prec = HISQ_F64;
 }
 
 static int check_solver(hisq_ctx* ctx, const void* x, const void* b, double mass, int maxiter,
@@ -985,8 +988,11 @@ static int check_solver(hisq_ctx* ctx, const void* x, const void* b, double mass
   if ((uintptr_t)x % 16 || (uintptr_t)b % 16) return set_error(HISQ_EINVAL, "vectors must be 16-byte aligned");
   hisq_solver_opts_default(o);
   if (opts) *o = *opts;
-  if (o->inner_prec < 0 || o->inner_prec > 3 || !ctx->links[o->inner_prec])
+  if (o->inner_prec < 0 || o->inner_prec >= NPREC || !ctx->links[o->inner_prec])
     return set_error(HISQ_EINVAL, "inner precision %d not resident", o->inner_prec);
+  if ((o->reliable_prec != HISQ_F64 && o->reliable_prec != HISQ_DF64) || !ctx->links[o->reliable_prec])
+    return set_error(HISQ_EINVAL, "reliable-update precision %d must be HISQ_F64 or a resident HISQ_DF64",
+                     o->reliable_prec);
   if (o->reliable_period < 1 || o->poll_every < 1) return set_error(HISQ_EINVAL, "periods must be >= 1");
   return HISQ_OK;
 }
@@ -1032,7 +1038,7 @@ int hisq_cg(hisq_ctx* ctx, double* x, const double* b, int nrhs, double mass, do
   if ((rc = stage_solver(ctx, x, b, vb, vb, true, &s)) != HISQ_OK) return rc;
   std::vector<double> tol(nrhs, rel_tol);
   const long long l0 = ctx->launches;
-  if (o.inner_prec == HISQ_F64)
+  if (o.inner_prec == HISQ_F64 || o.inner_prec == HISQ_DF64)
     rc = run_cg<double>(ctx, s.x, s.b, n, nrhs, mass, nullptr, tol.data(), maxiter, o, stats);
   else
     rc = run_cg<float>(ctx, s.x, s.b, n, nrhs, mass, nullptr, tol.data(), maxiter, o, stats);
@@ -1055,7 +1061,7 @@ int hisq_multishift_cg(hisq_ctx* ctx, double* x, const double* b, int nshift, co
   if ((rc = stage_solver(ctx, x, b, (size_t)nshift * n * sizeof(double2), n * sizeof(double2), false, &s)) != HISQ_OK)
     return rc;
   const long long l0 = ctx->launches;
-  if (o.inner_prec == HISQ_F64)
+  if (o.inner_prec == HISQ_F64 || o.inner_prec == HISQ_DF64)
     rc = run_multishift<double>(ctx, s.x, s.b, nshift, shifts, mass, rel_tol, maxiter, o, stats);
   else
     rc = run_multishift<float>(ctx, s.x, s.b, nshift, shifts, mass, rel_tol, maxiter, o, stats);

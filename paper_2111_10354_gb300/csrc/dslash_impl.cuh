@@ -10,6 +10,8 @@
 // their chunk planes; neighbour vectors go through L1/L2, where the 16-fold reuse of
 // each input site is served. Accumulation is FP64 for FP64 storage and FP32 otherwise.
 #pragma once
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace hisq {
@@ -72,7 +74,8 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const char* links, si
   // groups of 8 vectors keep the direction loop rolled: the fully unrolled body (16 hops x 8 vectors)
   // outgrows the instruction cache and the warps stall on instruction fetch (48^3x12 FP32: 260 -> 245 us;
   // FP16: 204 -> 183 us); at 4 vectors the unrolled body is faster (156 vs 171 us)
-  constexpr int MU_UNROLL = NR >= 8 ? 1 : 4;
+  // double-float keeps it rolled as well (its hoisted link loads otherwise exceed the register budget)
+  constexpr int MU_UNROLL = (NR >= 8 || std::is_same<LR, df64>::value) ? 1 : 4;
 #pragma unroll MU_UNROLL
   for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
@@ -148,6 +151,13 @@ struct DslashBounds {
   // FP32/16-bit: 64 registers for one vector, 128 for groups of 4 and 8 (enough warps in flight)
   static constexpr int min_blocks = sizeof(LR) == 8 ? 1 : (NR == 1 ? 4 : (NR == 2 ? 1 : (NR == 4 ? 2 : (NR == 8 ? 4 : 1))));
 };
+// Double-float: 128 registers for one vector (a double-float link is 36 registers), all 255 for
+// groups, where fewer spill.
+template <int NR>
+struct DslashBounds<df64, NR> {
+  static constexpr int threads = NR == 1 ? 256 : 128;
+  static constexpr int min_blocks = NR == 1 ? 2 : 1;
+};
 
 // TS threads share one output site, each applying its links to NR of the site's NR*TS vectors
 // (thread sub = threadIdx.x % TS takes vectors sub*NR .. sub*NR+NR-1). The TS lanes of a site sit in
@@ -185,13 +195,15 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
 #pragma unroll
         for (int i = 0; i < 3; ++i) o[i] = {SA(acc[r][i].re), SA(acc[r][i].im)};
       } else {
+        // the axpy in the accumulation type (FP64 for double-float: one FMA per entry)
+        using EA = typename std::conditional<std::is_same<A, df64>::value, double, A>::type;
         cplx<SA> yv[3];
         VecIO<SR>::load(y, site, yv);
-        const A a = A(k.a[rbase + r]);
+        const EA a = EA(k.a[rbase + r]);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          o[i].re = SA(fma(a, A(yv[i].re), -acc[r][i].re));
-          o[i].im = SA(fma(a, A(yv[i].im), -acc[r][i].im));
+          o[i].re = SA(fma(a, EA(yv[i].re), -EA(acc[r][i].re)));
+          o[i].im = SA(fma(a, EA(yv[i].im), -EA(acc[r][i].im)));
         }
         if (k.partials) {
           // the site's term in the arithmetic precision, summed over sites in FP64 (GB300's

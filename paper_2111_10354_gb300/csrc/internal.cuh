@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/hisq.h"
+#include "df64.cuh"
 
 namespace hisq {
 
@@ -70,8 +71,18 @@ struct Real<__nv_bfloat16> {
   using acc = float;
   static constexpr int prec = HISQ_BF16;
 };
+template <>
+struct Real<df64> {
+  using acc = df64;
+  static constexpr int prec = HISQ_DF64;
+};
 
-__host__ __device__ inline size_t real_size(int prec) { return prec == HISQ_F64 ? 8 : prec == HISQ_F32 ? 4 : 2; }
+constexpr int NPREC = 5;  // HISQ_F64 .. HISQ_DF64
+
+// Bytes per real of a precision's storage (HISQ_DF64: two FP32 words per real).
+__host__ __device__ inline size_t real_size(int prec) {
+  return (prec == HISQ_F64 || prec == HISQ_DF64) ? 8 : prec == HISQ_F32 ? 4 : 2;
+}
 
 // ------------------------------------------------------------------ geometry
 struct Geom {
@@ -209,6 +220,29 @@ struct LinkIO<float> {
                                              (float)U[2 * j + 1].im);
     float2* q = reinterpret_cast<float2*>(blk + (size_t)64 * half);
     q[cb] = make_float2((float)U[8].re, (float)U[8].im);
+  }
+};
+
+// Double-float links: entry k of every site is one float4 (re.hi, re.lo, im.hi, im.lo) in plane k,
+// 16 bytes like FP64. The split is round-to-nearest in both parts (|u - hi - lo| <= 2^-48 |u|).
+template <>
+struct LinkIO<df64> {
+  __device__ __forceinline__ static void load(const char* blk, int half, int cb, cplx<df64> U[9]) {
+    const float4* p = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 v = ld_stream(p + (size_t)k * half + cb);
+      U[k] = {df64(v.x, v.y), df64(v.z, v.w)};
+    }
+  }
+  __device__ __forceinline__ static void store(char* blk, int half, int cb, const cplx<double> U[9]) {
+    float4* p = reinterpret_cast<float4*>(blk);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float rh = __double2float_rn(U[k].re), ih = __double2float_rn(U[k].im);
+      p[(size_t)k * half + cb] = make_float4(rh, __double2float_rn(U[k].re - (double)rh), ih,
+                                             __double2float_rn(U[k].im - (double)ih));
+    }
   }
 };
 
@@ -487,7 +521,7 @@ struct hisq_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   unsigned prec_mask = 0;
-  char* links[4] = {nullptr, nullptr, nullptr, nullptr};  // per precision, 16 blocks each
+  char* links[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // per precision, 16 blocks each
   std::vector<unsigned char> t_loaded;                    // per t-slice
   unsigned load_flags = 0;
   bool links_ready = false;
@@ -500,7 +534,7 @@ struct hisq_ctx {
   int* d_flag = nullptr;             // device error flag
   long long launches = 0;            // kernels executed (eager + graph nodes)
   double naik = 0.0;                 // != 0: long links also stored compressed (two rows), see below
-  char* long12[4] = {nullptr, nullptr, nullptr, nullptr};  // per low precision, 8 blocks (parity, mu)
+  char* long12[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // per low precision, 8 blocks (parity, mu)
   bool capturing = false;            // inside this library's own stream capture
 };
 

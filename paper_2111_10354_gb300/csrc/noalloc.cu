@@ -48,13 +48,13 @@ using namespace hisq;
 extern "C" int hisq_apply_A_noalloc(hisq_ctx* c, void* out, const void* in, double mass, double sigma, int prec,
                                     int nrhs) {
   if (!c) return set_error(HISQ_EINVAL, "null context");
-  if (prec < 0 || prec > 3 || !c->links[prec]) return set_error(HISQ_EINVAL, "precision %d not resident", prec);
+  if (prec < 0 || prec >= NPREC || !c->links[prec]) return set_error(HISQ_EINVAL, "precision %d not resident", prec);
   if (nrhs < 1 || nrhs > 64) return set_error(HISQ_EINVAL, "nrhs %d outside [1, 64]", nrhs);
   if (!c->links_ready) return set_error(HISQ_ENOLINKS, "links not loaded");
   if (!out || !in || out == in) return set_error(HISQ_EINVAL, "null or aliased vectors");
   if (!is_device_ptr(out) || !is_device_ptr(in))
     return set_error(HISQ_EINVAL, "hisq_apply_A_noalloc takes device vectors only (host staging would allocate)");
-  const size_t align = prec == HISQ_F64 ? 16 : prec == HISQ_F32 ? 8 : 4;
+  const size_t align = (prec == HISQ_F64 || prec == HISQ_DF64) ? 16 : prec == HISQ_F32 ? 8 : 4;
   if ((uintptr_t)out % align || (uintptr_t)in % align) return set_error(HISQ_EINVAL, "misaligned vector");
   if (!(mass >= 0) || !(sigma >= 0)) return set_error(HISQ_EINVAL, "mass and sigma must be >= 0");
   const size_t need = (size_t)nrhs * c->g.half * 6 * real_size(prec);

@@ -10,22 +10,23 @@ from test_oracle_solvers import fft_solve
 pytestmark = pytest.mark.gpu
 
 
-def lattice(hisq, L, seed, eps=0.3, precs=(0, 1, 2, 3)):
+def lattice(hisq, L, seed, eps=0.3, precs=(0, 1, 2, 3, 4)):
     fat, lng = hin.gen_links(L, seed, eps, 0.1)
     lat = hisq.Lattice(L, precs=precs).load(fat, lng)
     ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
     return lat, ff, lf
 
 
-@pytest.mark.parametrize("inner", [0, 1, 2, 3])
-def test_cg_8444_plain_method(hisq, inner):
-    """8^4, m = 0.1, eps = 0.3 links, Gaussian source, to relative residual 1e-10."""
+@pytest.mark.parametrize("inner,rel", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (4, 4), (1, 4), (2, 4)])
+def test_cg_8444_plain_method(hisq, inner, rel):
+    """8^4, m = 0.1, eps = 0.3 links, Gaussian source, to relative residual 1e-10; inner 4 is plain CG with
+    the double-float operator, rel 4 takes the reliable updates and true residuals in double-float."""
     import torch
     L = (8, 8, 8, 8)
     lat, ff, lf = lattice(hisq, L, 1000)
     b = hin.gen_source(2000, lat.half, 1)
     x = torch.zeros((1, lat.half, 3), dtype=torch.complex128, device="cuda")
-    rc, st = lat.cg(x, torch.from_numpy(b).cuda(), 0.1, 1e-10, 2000, inner_prec=inner)
+    rc, st = lat.cg(x, torch.from_numpy(b).cuda(), 0.1, 1e-10, 2000, inner_prec=inner, reliable_prec=rel)
     assert rc == 0 and st["converged"] == 1
     xs = x.cpu().numpy()[0]
     r_oracle = oracle.true_residual(L, ff, lf, 0.1, b[0], xs)
@@ -33,7 +34,7 @@ def test_cg_8444_plain_method(hisq, inner):
     assert abs(r_oracle - st["true_rel_residual"]) < 1e-11
     x_ref, _ = oracle.cg(L, ff, lf, 0.1, b[0], tol=1e-12)
     assert np.linalg.norm(xs - x_ref) / np.linalg.norm(x_ref) < 1e-8
-    if inner != 0:
+    if inner not in (0, 4):
         assert st["reliable_updates"] >= 1
 
 
@@ -102,6 +103,12 @@ def test_cg_errors(hisq):
     assert e.value.code == hisq.HISQ_EINVAL
     with pytest.raises(hisq.HisqError) as e:
         lat.cg(x, b, 0.1, 1e-10, 100, inner_prec=2)  # FP16 links not resident
+    assert e.value.code == hisq.HISQ_EINVAL
+    with pytest.raises(hisq.HisqError) as e:
+        lat.cg(x, b, 0.1, 1e-10, 100, inner_prec=1, reliable_prec=4)  # double-float links not resident
+    assert e.value.code == hisq.HISQ_EINVAL
+    with pytest.raises(hisq.HisqError) as e:
+        lat.cg(x, b, 0.1, 1e-10, 100, inner_prec=1, reliable_prec=1)  # reliable updates need FP64-class
     assert e.value.code == hisq.HISQ_EINVAL
     rc, st = hisq.hisq_cg(lat.ctx, x, b, 1, 0.001, 1e-12, 3, hisq.make_opts(poll_every=1), raise_on_error=False)
     assert rc == hisq.HISQ_ENOCONV and st["converged"] == 0

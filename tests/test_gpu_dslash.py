@@ -1,6 +1,8 @@
 """GPU Dslash and A = 4m^2 - D_eo D_oe against the FP64 oracle, element by element, through the C ABI.
 
-Tolerance (relative global L2 over the whole output): FP64 1e-12, FP32 2e-6, FP16/BF16 5e-3.
+Tolerance (relative global L2 over the whole output): FP64 1e-12, FP32 2e-6, FP16/BF16 5e-3; the
+double-float precision (prec 4: FP64 vectors, links as FP32 pairs, 2^-47 rounding per operation) is held
+to the FP64 tolerance.
 Lattices: 8^4 (the plain-method workload), 8x10x12x14 (every hop distinct, ragged last block),
 4x6x8x10 (hops alias and must accumulate), 16^3x8 (several tiles).
 """
@@ -12,7 +14,8 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 2e-6, 2: 5e-3, 3: 5e-3}
+TOL = {0: 1e-12, 1: 2e-6, 2: 5e-3, 3: 5e-3, 4: 1e-12}
+F64_LAYOUT = (0, 4)  # precisions whose boundary vectors are complex128
 LATTICES = [(8, 8, 8, 8), (8, 10, 12, 14), (4, 6, 8, 10), (16, 16, 16, 8)]
 
 
@@ -20,7 +23,7 @@ def to_device(vec, prec):
     """complex128 numpy (nrhs, half, 3) -> torch tensor in the boundary layout of prec."""
     import torch
     t = torch.from_numpy(np.ascontiguousarray(vec))
-    if prec == 0:
+    if prec in F64_LAYOUT:
         return t.cuda()
     if prec == 1:
         return t.to(torch.complex64).cuda()
@@ -31,14 +34,14 @@ def to_device(vec, prec):
 def from_device(t, prec):
     import torch
     t = t.cpu()
-    if prec >= 2:
+    if prec in (2, 3):
         t = torch.view_as_complex(t.float().contiguous())
     return t.to(torch.complex128).numpy()
 
 
 def empty_like_prec(shape, prec):
     import torch
-    if prec == 0:
+    if prec in F64_LAYOUT:
         return torch.empty(shape, dtype=torch.complex128, device="cuda")
     if prec == 1:
         return torch.empty(shape, dtype=torch.complex64, device="cuda")
@@ -56,14 +59,14 @@ def setup(hisq, L, seed=1000):
     key = (L, seed)
     if key not in _cache:
         fat, lng = hin.gen_links(L, seed, 0.3, 0.1)
-        lat = hisq.Lattice(L).load(fat, lng)
+        lat = hisq.Lattice(L, precs=(0, 1, 2, 3, 4)).load(fat, lng)
         ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
         _cache[key] = (lat, ff, lf)
     return _cache[key]
 
 
 @pytest.mark.parametrize("L", LATTICES)
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("parity", [0, 1])
 def test_dslash_parity(hisq, L, prec, parity):
     lat, ff, lf = setup(hisq, L)
@@ -78,7 +81,7 @@ def test_dslash_parity(hisq, L, prec, parity):
 
 
 @pytest.mark.parametrize("nrhs", [2, 3, 4, 8, 16, 21])
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_dslash_multi_rhs(hisq, nrhs, prec):
     L = (8, 10, 12, 14)
     lat, ff, lf = setup(hisq, L)
@@ -93,7 +96,7 @@ def test_dslash_multi_rhs(hisq, nrhs, prec):
         assert rel_err(got[r], ref) <= TOL[prec], (nrhs, prec, r)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_apply_A_parity(hisq, prec):
     L = (8, 10, 12, 14)
     lat, ff, lf = setup(hisq, L)
@@ -180,6 +183,25 @@ def test_errors(hisq):
     with pytest.raises(hisq.HisqError) as e:
         lat.dslash(0, x, x, 0, 1)  # aliased
     assert e.value.code == hisq.HISQ_EINVAL
+
+
+def test_double_float_close_to_fp64(hisq):
+    """The double-float operator agrees with the FP64 one far inside the FP64 tolerance, on sources spanning
+    twelve decades (and exact zeros), whose conversion to double-float is done with integer operations."""
+    import torch
+    L = (8, 10, 12, 14)
+    lat, ff, lf = setup(hisq, L)
+    src = hin.gen_source(9100, lat.half, 1)
+    rng = np.random.default_rng(5)
+    src = src * 10.0 ** rng.uniform(-6, 6, size=src.shape)
+    src[0, ::7, 1] = 0.0
+    x = torch.from_numpy(src).cuda()
+    y64, ydf = torch.empty_like(x), torch.empty_like(x)
+    lat.dslash(0, y64, x, 0)
+    lat.dslash(0, ydf, x, 4)
+    ref = oracle.dslash(L, ff, lf, 0, src[0])
+    assert rel_err(ydf.cpu().numpy()[0], ref) <= 1e-13
+    assert rel_err(ydf.cpu().numpy()[0], y64.cpu().numpy()[0]) <= 1e-13
 
 
 def test_slab_loading_matches_whole(hisq):
