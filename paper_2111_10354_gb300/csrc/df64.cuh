@@ -84,4 +84,37 @@ __device__ __forceinline__ df64 operator+(const df64& a, const df64& b) {
   return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 
+// Two double-float numbers side by side (lane x, lane y), for Blackwell's two-wide FP32 instructions
+// (one FFMA2/FADD2/FMUL2 does the same operation on both lanes): a complex multiply-accumulate
+// updates the real and imaginary parts of its accumulator in the two lanes at once.
+struct df64x2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 df2_sub(float2 a, float2 b) {  // a - b, one rounding (b * -1 is exact)
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+__device__ __forceinline__ df64x2 df2_two_sum(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  const float2 bv = df2_sub(s, a);
+  return {s, __fadd2_rn(df2_sub(a, df2_sub(s, bv)), df2_sub(b, bv))};
+}
+
+__device__ __forceinline__ df64x2 df2_fast_two_sum(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  return {s, df2_sub(b, df2_sub(s, a))};
+}
+
+// Lane-wise a * b + c, the same steps as the scalar fma above.
+__device__ __forceinline__ df64x2 df2_fma(const df64x2& a, const df64x2& b, const df64x2& c) {
+  const float2 p = __fmul2_rn(a.hi, b.hi);
+  float2 pe = __ffma2_rn(a.hi, b.hi, make_float2(-p.x, -p.y));
+  pe = __ffma2_rn(a.hi, b.lo, pe);
+  pe = __ffma2_rn(a.lo, b.hi, pe);
+  const df64x2 s = df2_two_sum(c.hi, p);
+  const float2 t = __fadd2_rn(s.lo, __fadd2_rn(c.lo, pe));
+  return df2_fast_two_sum(s.hi, t);
+}
+
 }  // namespace hisq

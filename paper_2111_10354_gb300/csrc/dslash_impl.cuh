@@ -25,6 +25,18 @@ __device__ __forceinline__ void cmac_conj_sub(cplx<T>& acc, const cplx<T>& a, co
   acc.im = fma(a.im, b.re, acc.im);
 }
 
+// acc -= conj(a) * b in double-float on lane pairs: (re, im) += (-a.re, -a.re) (b.re, b.im)
+// + (-a.im, a.im) (b.im, b.re).
+__device__ __forceinline__ void cmac_conj_sub(cplx<df64>& acc, const cplx<df64>& a, const cplx<df64>& b) {
+  df64x2 c{make_float2(acc.re.hi, acc.im.hi), make_float2(acc.re.lo, acc.im.lo)};
+  c = df2_fma({make_float2(-a.re.hi, -a.re.hi), make_float2(-a.re.lo, -a.re.lo)},
+              {make_float2(b.re.hi, b.im.hi), make_float2(b.re.lo, b.im.lo)}, c);
+  c = df2_fma({make_float2(-a.im.hi, a.im.hi), make_float2(-a.im.lo, a.im.lo)},
+              {make_float2(b.im.hi, b.re.hi), make_float2(b.im.lo, b.re.lo)}, c);
+  acc.re = df64(c.hi.x, c.lo.x);
+  acc.im = df64(c.hi.y, c.lo.y);
+}
+
 struct DslashKArgs {
   Geom g;
   const char* links;  // resident link storage of the link precision (16 blocks)
