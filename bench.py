@@ -226,10 +226,30 @@ def vec_like(torch, half, prec, nrhs=1, seed=5):
     return r.to(torch.float16 if prec == 2 else torch.bfloat16).contiguous().cuda()
 
 
+def antiherm_rel(torch, lat, prec):
+    """|<u, D_eo v> + <D_oe u, v>| / |<u, D_eo v>| for random u, v: zero up to rounding for any correct
+    operator at any lattice size (the check the sweep records where the oracle cannot be run)."""
+    u, v = vec_like(torch, lat.half, prec, 1, seed=11), vec_like(torch, lat.half, prec, 1, seed=12)
+    Dv, Du = torch.empty_like(v), torch.empty_like(u)
+    torch.cuda.synchronize()  # inputs were written on torch's stream, the library runs on its own
+    lat.dslash(0, Dv, v, prec, 1)
+    lat.dslash(1, Du, u, prec, 1)
+    torch.cuda.synchronize()
+
+    def c128(t):
+        if t.dtype in (torch.float16, torch.bfloat16):
+            t = torch.view_as_complex(t.float().contiguous())
+        return t.to(torch.complex128).flatten()
+    lhs = complex(torch.vdot(c128(u), c128(Dv)))
+    rhs = -complex(torch.vdot(c128(Du), c128(v)))
+    return abs(lhs - rhs) / abs(lhs)
+
+
 def time_dslash(torch, lat, prec, nrhs, reps, stream):
     """Average device time of one Dslash launch (alternating D_oe, D_eo) with CUDA events on its stream."""
     x = vec_like(torch, lat.half, prec, nrhs)
     y, z = torch.empty_like(x), torch.empty_like(x)
+    torch.cuda.synchronize()  # x was written on torch's stream
     with torch.cuda.stream(stream):
         for _ in range(3):
             lat.dslash(1, y, x, prec, nrhs)
@@ -269,6 +289,7 @@ def run_ours(args, rank, world, local):
     half = lat.half
     b = torch.from_numpy(b_np).cuda()
     x = torch.zeros_like(b)
+    torch.cuda.synchronize()  # b and x were written on torch's stream; the solves run on the library's
     opts = dict(inner_prec=h.HISQ_F32, reliable_period=50)
 
     def solve(xv, bv, **o):
@@ -342,6 +363,7 @@ def run_ours(args, rank, world, local):
                         ("fp64", dict(inner_prec=h.HISQ_F64)), ("df64", dict(inner_prec=h.HISQ_DF64)),
                         ("mixed_f32_df64_reliable", dict(inner_prec=h.HISQ_F32, reliable_prec=h.HISQ_DF64))):
             xs = torch.zeros_like(b)
+            torch.cuda.synchronize()
             lat.cg(xs, b, m, TOL, 20000, **o)  # first call tunes this variant's kernels
             xs.zero_()
             torch.cuda.synchronize()
@@ -356,6 +378,7 @@ def run_ours(args, rank, world, local):
         for name, o in (("mixed_f32_comp12", dict(inner_prec=h.HISQ_F32)),
                         ("mixed_f16_comp12", dict(inner_prec=h.HISQ_F16))):
             xs = torch.zeros_like(b)
+            torch.cuda.synchronize()
             lat.cg(xs, b, m, TOL, 20000, **o)  # first call tunes the compressed kernels
             xs.zero_()
             torch.cuda.synchronize()
@@ -430,11 +453,14 @@ def run_sweep():
             for nrhs in ((1, 4, 8, 16) if p == h.HISQ_F32 and L == (48, 48, 48, 12) else (1,)):
                 ms = time_dslash(torch, lat, p, nrhs, 20, stream)
                 by = lat.dslash_bytes(p, nrhs)
-                print(json.dumps({"lattice": "x".join(map(str, L)), "prec": h.PREC_NAMES[p], "nrhs": nrhs,
-                                  "us": round(ms * 1e3, 2), "GB/s": round(by / ms / 1e6, 1),
-                                  "frac_hbm": round(by / ms / 1e6 / peak, 3),
-                                  "sites_per_s": round(nrhs * V / 2 / (ms * 1e-3), 1),
-                                  "GFLOP/s": round(1146 * nrhs * V / 2 / (ms * 1e-3) / 1e9, 1)}), flush=True)
+                line = {"lattice": "x".join(map(str, L)), "prec": h.PREC_NAMES[p], "nrhs": nrhs,
+                        "us": round(ms * 1e3, 2), "GB/s": round(by / ms / 1e6, 1),
+                        "frac_hbm": round(by / ms / 1e6 / peak, 3),
+                        "sites_per_s": round(nrhs * V / 2 / (ms * 1e-3), 1),
+                        "GFLOP/s": round(1146 * nrhs * V / 2 / (ms * 1e-3) / 1e9, 1)}
+                if nrhs == 1:
+                    line["antiherm_rel"] = float("%.3g" % antiherm_rel(torch, lat, p))
+                print(json.dumps(line), flush=True)
         # the tuner's choice per kernel: variant * 10000 + block (1-vector forms: variant 1 = z-slowest walk)
         print(json.dumps({"lattice": "x".join(map(str, L)), "tuned": h.hisq_tune_report(lat.ctx).splitlines()}),
               flush=True)
@@ -473,6 +499,7 @@ def row_multirhs(h, torch, hin):
         by = lat.dslash_bytes(h.HISQ_F32, n)
         b = torch.from_numpy(hin.gen_source(2002, lat.half, n)).cuda()
         x = torch.zeros_like(b)
+        torch.cuda.synchronize()  # inputs come from torch's stream, the solve runs on the library's
         lat.cg(x, b, 0.01, 1e-10, 5000, nrhs=n, inner_prec=h.HISQ_F32)  # warm-up / tuning
         x.zero_()
         dt, (rc, st) = _timed(torch, lambda: lat.cg(x, b, 0.01, 1e-10, 5000, nrhs=n, inner_prec=h.HISQ_F32))
@@ -494,6 +521,7 @@ def row_multishift(h, torch, hin):
     shifts = np.logspace(-5, 0, 14)
     b = torch.from_numpy(hin.gen_source(2002, lat.half, 1)).cuda()
     x = torch.zeros((14, lat.half, 3), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()  # inputs come from torch's stream, the solve runs on the library's
     for name, prec in (("fp32_krylov+refine", h.HISQ_F32), ("fp64", h.HISQ_F64)):
         lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 20000, inner_prec=prec)
         dt, (rc, st) = _timed(torch, lambda: lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 20000, inner_prec=prec))
@@ -524,6 +552,7 @@ def row_batch(h, torch, hin):
     b = torch.from_numpy(np.concatenate([v.reshape(-1) for v in bs]).reshape(-1, 3)).cuda()
     masses = [m["mass"] for m in mix]
     x = torch.zeros_like(b)
+    torch.cuda.synchronize()  # inputs come from torch's stream, the solve runs on the library's
     for name, prec in (("batched mixed f32/f64", h.HISQ_F32), ("batched fp64", h.HISQ_F64)):
         batch.cg(x, b, masses, 1e-10, 10000, inner_prec=prec)
         x.zero_()
@@ -567,6 +596,7 @@ def row_learned(h, torch, hin, epochs=6, batch_pairs=16):
     for i, lat in enumerate(train):
         b = torch.from_numpy(hin.gen_source(5000 + i, half, 128)).cuda()
         x = torch.zeros_like(b)
+        torch.cuda.synchronize()  # inputs come from torch's stream, the solve runs on the library's
         for k in range(0, 128, 16):  # 16 sources per link read
             lat.cg(x[k:k + 16], b[k:k + 16], mass, 1e-10, 20000, nrhs=16, inner_prec=h.HISQ_F32)
         pairs.append((b.to(torch.complex64), x.to(torch.complex64)))
@@ -597,10 +627,12 @@ def row_learned(h, torch, hin, epochs=6, batch_pairs=16):
         net.bind(lat)
         b = torch.from_numpy(hin.gen_source(6000 + i, half, 1)).cuda()
         x = torch.zeros_like(b)
+        torch.cuda.synchronize()  # inputs come from torch's stream, the solve runs on the library's
         net.fcg(x, b, mass, 1e-10, 20000)
         x.zero_()
         dt_f, (rc_f, st_f) = _timed(torch, lambda: net.fcg(x, b, mass, 1e-10, 20000))
         x2 = torch.zeros_like(b)
+        torch.cuda.synchronize()
         lat.cg(x2, b, mass, 1e-10, 20000, inner_prec=h.HISQ_F32)
         x2.zero_()
         dt_c, (rc_c, st_c) = _timed(torch, lambda: lat.cg(x2, b, mass, 1e-10, 20000, inner_prec=h.HISQ_F32))
@@ -658,6 +690,7 @@ def run_kernel_case(name):
         net.set_weights(W1, optc.tie(W1))
         r = torch.from_numpy(hin.gen_source(1, lat.half, 1)).to(torch.complex64).cuda()
         z = torch.empty_like(r)
+        torch.cuda.synchronize()  # r comes from torch's stream, the network runs on the library's
         for _ in range(4):
             net.apply(z, r, 1)
         torch.cuda.synchronize()
@@ -672,6 +705,7 @@ def run_kernel_case(name):
             bs.append(hin.gen_source(m["source_seed"], int(np.prod(m["dims"])) // 2, 1)[0])
         b = torch.from_numpy(np.concatenate([v.reshape(-1) for v in bs]).reshape(-1, 3)).cuda()
         x = torch.zeros_like(b)
+        torch.cuda.synchronize()  # inputs come from torch's stream, the solve runs on the library's
         rc, st = batch.cg(x, b, [m["mass"] for m in mix], 1e-10, 10000, inner_prec=h.HISQ_F32)
         print(json.dumps({"case": name, "iters": st["iters"]}))
 
