@@ -71,8 +71,9 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the device code the Dslash kernel is compiled from (kernel body, its helpers and types)."""
     h = hashlib.sha256()
-    for name in ("dslash_impl.cuh", "internal.cuh", "dslash_launch.cuh"):
+    for name in ("dslash_impl.cuh", "internal.cuh", "df64.cuh"):
         with open(os.path.join(ROOT, "paper_2111_10354_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -12,15 +12,15 @@ namespace hisq {
 // One launch form: NR vectors per thread, TS threads per site (NR * TS vectors per launch).
 template <typename LR, typename SR, int NR, int EPI, bool COMP, int TS>
 static TuneVariant dslash_variant(hisq_ctx* ctx, const DslashKArgs& a) {
-  auto kern = dslash_kernel<LR, SR, NR, EPI, COMP, TS>;
-  return TuneVariant{(const void*)kern, [ctx, &a, kern](int block) -> cudaError_t {
+  // the launcher captures two pointers only, so std::function keeps it without a heap allocation
+  return TuneVariant{(const void*)dslash_kernel<LR, SR, NR, EPI, COMP, TS>, [ctx, &a](int block) -> cudaError_t {
                        int grid = (int)(((size_t)ctx->g.half * TS + block - 1) / block);
                        // reducing launches: one wave of blocks keeps the partials (and the finishing
                        // block's tail) short
                        int cap = (EPI == EPI_AXPY && a.partials) ? ctx->num_sms * (2048 / block)
                                                                 : max_grid_blocks(ctx, block);
                        if (grid > cap) grid = cap;
-                       kern<<<grid, block, 0, ctx->stream>>>(a);
+                       dslash_kernel<LR, SR, NR, EPI, COMP, TS><<<grid, block, 0, ctx->stream>>>(a);
                        return cudaGetLastError();
                      }};
 }
