@@ -165,6 +165,11 @@ int pack_links_slab(hisq_ctx* ctx, const double* d_fat, const double* d_long, in
 }
 
 // ------------------------------------------------------------------ vector staging
+void release_graphs(hisq_ctx* ctx) {
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.first);
+  ctx->graphs.clear();
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -268,6 +273,7 @@ int hisq_destroy(hisq_ctx* c) {
     cudaFree(c->links[p]);
     cudaFree(c->long12[p]);
   }
+  release_graphs(c);
   for (auto& kv : c->ws) cudaFree(kv.second.ptr);
   cudaFree(c->d_counters);
   cudaFree(c->d_flag);
@@ -428,6 +434,7 @@ int hisq_set_long_compression(hisq_ctx* c, double naik) {
   if (!(naik == naik) || fabs(naik) > 1e6) return set_error(HISQ_EINVAL, "bad Naik coefficient");
   if (naik == c->naik) return HISQ_OK;
   cudaStreamSynchronize(c->stream);
+  release_graphs(c);  // captured Dslash launches carry the compression state
   for (int p = 1; p < 4; ++p) {
     cudaFree(c->long12[p]);
     c->long12[p] = nullptr;

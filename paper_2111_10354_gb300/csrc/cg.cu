@@ -475,47 +475,66 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   HISQ_CUDA(cudaMemcpyAsync(B.st, hst, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
   if ((rc = reliable<S>(ctx, B, nrhs, 1)) != HISQ_OK) return rc;
 
-  // pre-tune the inner Dslash launches outside any capture (they are idempotent)
-  {
-    DslashCall c1;
-    c1.out_parity = 1;
-    c1.out = B.t;
-    c1.in = B.p;
-    c1.nrhs = nrhs;
-    c1.rhs_stride = ctx->g.half;
-    if ((rc = dslash_launch(ctx, lp, sp, c1)) != HISQ_OK) return rc;
-    DslashCall c2 = c1;
-    c2.out_parity = 0;
-    c2.out = B.Ap;
-    c2.in = B.t;
-    c2.y = B.p;
-    c2.a_rhs = B.a.data();
-    c2.epi = EPI_AXPY;
-    c2.partials = B.partials + 2 * MAXR * partial_stride(ctx);
-    c2.dot_out = B.st->pAp;
-    c2.counter = ctx->d_counters + 3;
-    if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
-  }
-
   const int cycle = hst->cycle_limit;
   cudaGraphExec_t exec = nullptr;
   long long graph_nodes = 0;
   if (o.use_graph) {
-    cudaGraph_t graph;
-    HISQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    ctx->capturing = true;
-    int crc = HISQ_OK;
-    for (int i = 0; i < cycle && crc == HISQ_OK; ++i) crc = iteration<S>(ctx, B, lp, nrhs);
-    ctx->capturing = false;
-    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
-    if (crc != HISQ_OK) return crc;
-    HISQ_CUDA(ce);
-    size_t nodes = 0;
-    cudaGraphGetNodes(graph, nullptr, &nodes);
-    graph_nodes = (long long)nodes;
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    HISQ_CUDA(ce);
+    // a cycle's graph depends on the buffers, shapes and per-rhs coefficients it was captured with
+    std::string key = "cg/" + std::to_string(sizeof(S)) + "/" + std::to_string(lp) + "/" + std::to_string(nrhs) +
+                      "/" + std::to_string(cycle);
+    char buf[64];
+    for (const void* ptr : {(const void*)B.r, (const void*)B.p, (const void*)B.Ap, (const void*)B.t,
+                            (const void*)B.e, (const void*)B.st, (const void*)B.partials}) {
+      snprintf(buf, sizeof buf, "/%p", ptr);
+      key += buf;
+    }
+    for (double a : B.a) {
+      snprintf(buf, sizeof buf, "/%a", a);
+      key += buf;
+    }
+    auto cached = ctx->graphs.find(key);
+    if (cached != ctx->graphs.end()) {
+      exec = cached->second.first;
+      graph_nodes = cached->second.second;
+    } else {
+      // tune the inner Dslash launches outside the capture (they are idempotent)
+      DslashCall c1;
+      c1.out_parity = 1;
+      c1.out = B.t;
+      c1.in = B.p;
+      c1.nrhs = nrhs;
+      c1.rhs_stride = ctx->g.half;
+      if ((rc = dslash_launch(ctx, lp, sp, c1)) != HISQ_OK) return rc;
+      DslashCall c2 = c1;
+      c2.out_parity = 0;
+      c2.out = B.Ap;
+      c2.in = B.t;
+      c2.y = B.p;
+      c2.a_rhs = B.a.data();
+      c2.epi = EPI_AXPY;
+      c2.partials = B.partials + 2 * MAXR * partial_stride(ctx);
+      c2.dot_out = B.st->pAp;
+      c2.counter = ctx->d_counters + 3;
+      if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
+
+      cudaGraph_t graph;
+      HISQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      ctx->capturing = true;
+      int crc = HISQ_OK;
+      for (int i = 0; i < cycle && crc == HISQ_OK; ++i) crc = iteration<S>(ctx, B, lp, nrhs);
+      ctx->capturing = false;
+      cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+      if (crc != HISQ_OK) return crc;
+      HISQ_CUDA(ce);
+      size_t nodes = 0;
+      cudaGraphGetNodes(graph, nullptr, &nodes);
+      graph_nodes = (long long)nodes;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      HISQ_CUDA(ce);
+      if (ctx->graphs.size() >= 32) release_graphs(ctx);  // bound the cache
+      ctx->graphs[key] = {exec, graph_nodes};
+    }
   }
   auto run_cycle = [&]() -> int {
     if (exec) {
@@ -581,7 +600,6 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
       note_launch(ctx);
     }
   }
-  if (exec) cudaGraphExecDestroy(exec);
   if (!verified) {
     // the iterate changed since the last true residual: recompute it for the report
     if ((rc = fold()) != HISQ_OK) return rc;
@@ -866,37 +884,65 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
   HISQ_CUDA(cudaGetLastError());
   note_launch(ctx);
   const double a_base = 4.0 * mass * mass + shifts[base];
-  // pre-tune outside capture
-  {
-    DslashCall c1;
-    c1.out_parity = 1;
-    c1.out = t;
-    c1.in = p + (size_t)base * n * 2;
-    c1.nrhs = 1;
-    c1.rhs_stride = ctx->g.half;
-    int rc = dslash_launch(ctx, lp, sp, c1);
-    if (rc != HISQ_OK) return rc;
-  }
   const int cycle = o.poll_every;
   cudaGraphExec_t exec = nullptr;
   long long graph_nodes = 0;
   if (o.use_graph) {
-    cudaGraph_t graph;
-    HISQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    ctx->capturing = true;
-    int crc = HISQ_OK;
-    for (int i = 0; i < cycle && crc == HISQ_OK; ++i)
-      crc = ms_iteration<S>(ctx, lp, x, r, p, Ap, t, st, partials, a_base, base, ns);
-    ctx->capturing = false;
-    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
-    if (crc != HISQ_OK) return crc;
-    HISQ_CUDA(ce);
-    size_t nodes = 0;
-    cudaGraphGetNodes(graph, nullptr, &nodes);
-    graph_nodes = (long long)nodes;
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    HISQ_CUDA(ce);
+    std::string key = "ms/" + std::to_string(sizeof(S)) + "/" + std::to_string(lp) + "/" + std::to_string(ns) + "/" +
+                      std::to_string(base) + "/" + std::to_string(cycle);
+    char buf[64];
+    for (const void* ptr : {(const void*)x, (const void*)r, (const void*)p, (const void*)Ap, (const void*)t,
+                            (const void*)st, (const void*)partials}) {
+      snprintf(buf, sizeof buf, "/%p", ptr);
+      key += buf;
+    }
+    snprintf(buf, sizeof buf, "/%a", a_base);
+    key += buf;
+    auto cached = ctx->graphs.find(key);
+    if (cached != ctx->graphs.end()) {
+      exec = cached->second.first;
+      graph_nodes = cached->second.second;
+    } else {
+      // tune both Dslash launches of an iteration outside the capture (they are idempotent)
+      DslashCall c1;
+      c1.out_parity = 1;
+      c1.out = t;
+      c1.in = p + (size_t)base * n * 2;
+      c1.nrhs = 1;
+      c1.rhs_stride = ctx->g.half;
+      int rc = dslash_launch(ctx, lp, sp, c1);
+      if (rc != HISQ_OK) return rc;
+      DslashCall c2 = c1;
+      c2.out_parity = 0;
+      c2.out = Ap;
+      c2.in = t;
+      c2.y = c1.in;
+      c2.a = a_base;
+      c2.epi = EPI_AXPY;
+      c2.partials = partials + MAXR * partial_stride(ctx);
+      c2.dot_out = &st->pAp;
+      c2.counter = ctx->d_counters + 6;
+      if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
+
+      cudaGraph_t graph;
+      HISQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      ctx->capturing = true;
+      int crc = HISQ_OK;
+      for (int i = 0; i < cycle && crc == HISQ_OK; ++i)
+        crc = ms_iteration<S>(ctx, lp, x, r, p, Ap, t, st, partials, a_base, base, ns);
+      ctx->capturing = false;
+      cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+      if (crc != HISQ_OK) return crc;
+      HISQ_CUDA(ce);
+      size_t nodes = 0;
+      cudaGraphGetNodes(graph, nullptr, &nodes);
+      graph_nodes = (long long)nodes;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      HISQ_CUDA(ce);
+      if (ctx->graphs.size() >= 32) release_graphs(ctx);  // bound the cache
+      ctx->graphs[key] = {exec, graph_nodes};
+    }
   }
   int status = HISQ_OK;
   int last_iter = 0;
@@ -932,7 +978,6 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
     HISQ_CUDA(cudaMemcpyAsync(&st->done, &h->done, 2 * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
   }
-  if (exec) cudaGraphExecDestroy(exec);
   if (stats) {
     for (int k = 0; k < ns; ++k) stats->shift_iters[k] = h->conv_iter[k];
     stats->iters = h->iter;

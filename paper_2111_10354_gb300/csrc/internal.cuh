@@ -548,6 +548,9 @@ struct hisq_ctx {
   double naik = 0.0;                 // != 0: long links also stored compressed (two rows), see below
   char* long12[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // per low precision, 8 blocks (parity, mu)
   bool capturing = false;            // inside this library's own stream capture
+  // instantiated solver graphs, keyed by everything their kernels capture (buffers, shapes,
+  // coefficients), so repeated solves replay them instead of capturing again
+  std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;
 };
 
 namespace hisq {
@@ -562,6 +565,7 @@ int cuda_error(cudaError_t e, const char* what);
   } while (0)
 
 void* workspace(hisq_ctx* ctx, const char* name, size_t bytes);  // nullptr on failure
+void release_graphs(hisq_ctx* ctx);                               // destroy the cached solver graphs
 
 // Count one eager kernel launch (launches recorded into a graph are counted per replay).
 inline void note_launch(hisq_ctx* ctx, int n = 1) {

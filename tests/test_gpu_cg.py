@@ -118,3 +118,23 @@ def test_cg_errors(hisq):
     with pytest.raises(hisq.HisqError) as e:
         lat.cg(torch.zeros_like(b), bad, 0.1, 1e-10, 100)
     assert e.value.code == hisq.HISQ_ENONFINITE
+
+
+def test_cg_repeated_solves_reuse_graphs(hisq):
+    """Solves on one context replay cached graphs keyed by their coefficients and buffers: alternating masses
+    (different per-rhs diagonal captured in the graph) each meet their true residual, and repeating a solve
+    reproduces it bit for bit."""
+    import torch
+    L = (8, 10, 12, 14)
+    lat, ff, lf = lattice(hisq, L, 41)
+    b = hin.gen_source(42, lat.half, 1)
+    bt = torch.from_numpy(b).cuda()
+    xs = []
+    for mass in (0.1, 0.05, 0.1):
+        x = torch.zeros_like(bt)
+        rc, st = lat.cg(x, bt, mass, 1e-10, 5000, inner_prec=1)
+        assert rc == 0
+        assert oracle.true_residual(L, ff, lf, mass, b[0], x.cpu().numpy()[0]) <= 1e-10
+        xs.append(x.cpu())
+    assert torch.equal(xs[0], xs[2])
+    assert not torch.equal(xs[0], xs[1])
