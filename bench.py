@@ -154,10 +154,24 @@ def gen_workload(rank: int):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
+def omp_threads(n=None):
+    """Set (n given) and return the OpenMP thread count of the oracle's runtime (libgomp)."""
+    import ctypes
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    if n is not None:
+        gomp.omp_set_num_threads(int(n))
+    return int(gomp.omp_get_max_threads())
+
+
 def oracle_sample(fat, lng, b, target_s: float = 12.0):
     """The oracle's FP64 CG on the same lattice, bounded: enough iterations for ~target_s seconds.
     Returns (GB/s of Dslash algorithmic bytes at FP64, seconds, iterations, threads)."""
     import oracle
+    oracle.build()
+    threads = omp_threads()
     L = DIMS
     ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
     half = int(np.prod(L)) // 2
@@ -170,7 +184,6 @@ def oracle_sample(fat, lng, b, target_s: float = 12.0):
     dt = time.perf_counter() - t0
     n_dslash = 2 * (iters + 1)  # initial residual + one A per iteration
     bytes_ = n_dslash * half * (16 * 18 + 12) * 8.0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return bytes_ / dt / 1e9, dt, iters, threads
 
 
@@ -399,6 +412,13 @@ def run_ours(args, rank, world, local):
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                "sample": "oracle FP64 CG on 48x48x48x12 m=0.01: %d iterations (%d Dslash) in %.1f s" % (
                    it, 2 * (it + 1), dt)}
+        # the same oracle on one host core
+        all_threads = omp_threads()
+        omp_threads(1)
+        gbs1, dt1, it1, _ = oracle_sample(fat, lng, b_np, 5.0)
+        omp_threads(all_threads)
+        cpu["single_core"] = {"value": round(gbs1, 4), "unit": "GB/s", "cores": 1,
+                              "sample": "%d iterations (%d Dslash) in %.1f s" % (it1, 2 * (it1 + 1), dt1)}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
