@@ -52,7 +52,7 @@ def parse():
                     help="time the steps only: no e2e, comparison solves or CPU baseline (for profiler launch lists)")
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
     ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-df64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8",
-                                                   "ptc", "batch"],
+                                                   "cg-f32-nr8", "ptc", "batch"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
@@ -344,9 +344,11 @@ def run_ours(args, rank, world, local):
             dist.destroy_process_group()
         return
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    b_host = np.ascontiguousarray(b_np)
-    x_host = np.zeros_like(b_host)
+    # end to end through the C ABI with pinned host buffers (the library copies b and the initial x in
+    # and x out on its stream, inside the timed region)
+    b_pin = torch.from_numpy(np.ascontiguousarray(b_np)).pin_memory()
+    x_pin = torch.zeros_like(b_pin).pin_memory()
+    b_host, x_host = b_pin.numpy(), x_pin.numpy()
     barrier()
     t0 = time.perf_counter()
     e2e_bytes = 0.0
@@ -504,7 +506,7 @@ def row_multirhs(h, torch, hin):
     L = (48, 48, 48, 12)
     fat, lng = hin.gen_links(L, 1002, 0.3, 0.1)
     stream = torch.cuda.Stream()
-    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16), stream=stream).load(fat, lng)
+    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16, h.HISQ_DF64), stream=stream).load(fat, lng)
     peak, _ = peaks()
     # Dslash only at FP16 storage (FP32 arithmetic) and FP64
     for prec, name, ns in ((h.HISQ_F16, "f16", (1, 2, 4, 8, 16)), (h.HISQ_F64, "f64", (1, 2, 4, 8))):
@@ -528,6 +530,14 @@ def row_multirhs(h, torch, hin):
                           "dslash_us": round(ms * 1e3, 1), "dslash_GBps": round(by / ms / 1e6, 1),
                           "dslash_frac_hbm": round(by / ms / 1e6 / peak, 3),
                           "dslash_GFLOPs": round(1146 * n * lat.half / (ms * 1e-3) / 1e9, 1),
+                          "cg_s": round(dt, 4), "cg_s_per_rhs": round(dt / n, 4), "cg_iters": st["iters"],
+                          "worst_true_res": st["true_rel_residual"]}), flush=True)
+        # the same solve with double-float reliable updates (the FP64 Dslash of n vectors is FP64-pipe bound)
+        lat.cg(x, b, 0.01, 1e-10, 5000, nrhs=n, inner_prec=h.HISQ_F32, reliable_prec=h.HISQ_DF64)
+        x.zero_()
+        dt, (rc, st) = _timed(torch, lambda: lat.cg(x, b, 0.01, 1e-10, 5000, nrhs=n, inner_prec=h.HISQ_F32,
+                                                    reliable_prec=h.HISQ_DF64))
+        print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": "f32", "reliable": "df64", "nrhs": n,
                           "cg_s": round(dt, 4), "cg_s_per_rhs": round(dt / n, 4), "cg_iters": st["iters"],
                           "worst_true_res": st["true_rel_residual"]}), flush=True)
     # launch forms the tuner chose: key -> variant * 10000 + block (vectors per thread x threads per site)
@@ -700,6 +710,18 @@ def run_kernel_case(name):
                 "dslash-f32-nr8": h.HISQ_F32}[name]
         ms = time_dslash(torch, lat, prec, 8 if name.endswith("nr8") else 1, 4, stream)
         print(json.dumps({"case": name, "us": round(ms * 1e3, 2)}))
+    elif name == "cg-f32-nr8":
+        L = (48, 48, 48, 12)
+        fat, lng = hin.gen_links(L, 1002, 0.3, 0.1)
+        lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=stream).load(fat, lng)
+        b = torch.from_numpy(hin.gen_source(2002, lat.half, 8)).cuda()
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        for _ in range(2):  # the first solve tunes and captures, the second replays
+            x.zero_()
+            torch.cuda.synchronize()
+            rc, st = lat.cg(x, b, 0.01, 1e-10, 5000, nrhs=8, inner_prec=h.HISQ_F32)
+        print(json.dumps({"case": name, "iters": st["iters"], "s": round(st["seconds"], 4)}))
     elif name == "ptc":
         import oracle.ptc as optc
         L = (32, 32, 32, 8)
