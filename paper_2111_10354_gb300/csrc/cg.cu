@@ -183,7 +183,7 @@ __device__ __forceinline__ void store_k(X* v, size_t e, const cplx<typename Real
 // n: complex entries per rhs (3 * half).
 template <typename S, typename X>
 __global__ void __launch_bounds__(256, 6) k_update(X* __restrict__ x, S* __restrict__ r, const S* __restrict__ p, const S* __restrict__ Ap,
-                         size_t n, SolverState* st, double* partials, size_t pstride, unsigned* counter) {
+                         size_t n, SolverState* st, double* partials, size_t pstride, unsigned* row_counters) {
   if (st->done) return;
   using T = typename Real<S>::acc;
   using XT = typename Real<X>::acc;
@@ -222,13 +222,12 @@ __global__ void __launch_bounds__(256, 6) k_update(X* __restrict__ x, S* __restr
     for (int c = 0; c < K; ++c) t += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
     v[0] += (double)t;
   }
-  double out[1][MAXR];
-  if (grid_reduce<1>(v, partials, pstride, counter, out, st->nrhs) && threadIdx.x == 0) {
-    for (int q = 0; q < st->nrhs; ++q) {
-      st->rr_new[q] = out[0][q];
-      if (st->rhs_done[q]) continue;
-      if (!(st->pAp[q] > 0.0)) st->breakdown = 1;
-      if (!isfinite(out[0][q])) st->nonfinite = 1;
+  double tot;
+  if (row_reduce(v[0], partials, pstride, row_counters, &tot) && threadIdx.x == 0) {
+    st->rr_new[rh] = tot;
+    if (!st->rhs_done[rh]) {
+      if (!(pap > 0.0)) st->breakdown = 1;
+      if (!isfinite(tot)) st->nonfinite = 1;
     }
   }
 }
@@ -306,6 +305,7 @@ struct CgBuffers {
   SolverState* st;
   double* partials;
   int rp = HISQ_F64;     // operator precision of the true residual: HISQ_F64 or HISQ_DF64
+  unsigned* rowc;        // per-rhs block counters of the row reductions [MAXR]
 };
 
 static dim3 blas_grid(const hisq_ctx* ctx, int nrhs, size_t units, int per_sm = 8) {
@@ -383,10 +383,10 @@ static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
   dim3 grid = blas_grid(ctx, nrhs, n / Chunk<S>::K, 6);
   if constexpr (sizeof(S) == 8)
     k_update<S, double><<<grid, 256, 0, ctx->stream>>>((double*)B.x, (S*)B.r, (const S*)B.p, (const S*)B.Ap, n,
-                                                       B.st, B.partials, partial_stride(ctx), ctx->d_counters + 4);
+                                                       B.st, B.partials, partial_stride(ctx), B.rowc);
   else
     k_update<S, float><<<grid, 256, 0, ctx->stream>>>((float*)B.e, (S*)B.r, (const S*)B.p, (const S*)B.Ap, n,
-                                                      B.st, B.partials, partial_stride(ctx), ctx->d_counters + 4);
+                                                      B.st, B.partials, partial_stride(ctx), B.rowc);
   k_pupdate<S><<<blas_grid(ctx, nrhs, n / Chunk<S>::K, 8), 256, 0, ctx->stream>>>((const S*)B.r, (S*)B.p, n, B.st,
                                                                                ctx->d_counters + 5);
   HISQ_CUDA(cudaGetLastError());
@@ -422,10 +422,12 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   B.t = workspace(ctx, "cg_t", vbS);
   B.st = (SolverState*)workspace(ctx, "cg_state", sizeof(SolverState));
   B.partials = (double*)workspace(ctx, "cg_partials", 3 * MAXR * partial_stride(ctx) * sizeof(double));
+  B.rowc = (unsigned*)workspace(ctx, "cg_rowc", MAXR * sizeof(unsigned));
   B.e = mixed ? workspace(ctx, "cg_e", (size_t)nrhs * n * 2 * sizeof(float)) : (void*)x;
   SolverState* hst = (SolverState*)ctx->pinned;
-  if (!B.r_hi || !B.Ax || !B.t64 || !B.r || !B.p || !B.Ap || !B.t || !B.st || !B.partials || !B.e)
+  if (!B.r_hi || !B.Ax || !B.t64 || !B.r || !B.p || !B.Ap || !B.t || !B.st || !B.partials || !B.e || !B.rowc)
     return set_error(HISQ_ENOMEM, "solver workspace");
+  HISQ_CUDA(cudaMemsetAsync(B.rowc, 0, MAXR * sizeof(unsigned), ctx->stream));
   if (mixed) HISQ_CUDA(cudaMemsetAsync(B.e, 0, (size_t)nrhs * n * 2 * sizeof(float), ctx->stream));
   auto fold = [&]() -> int {
     if (!mixed) return HISQ_OK;

@@ -15,10 +15,15 @@ static TuneVariant dslash_variant(hisq_ctx* ctx, const DslashKArgs& a) {
   // the launcher captures two pointers only, so std::function keeps it without a heap allocation
   return TuneVariant{(const void*)dslash_kernel<LR, SR, NR, EPI, COMP, TS>, [ctx, &a](int block) -> cudaError_t {
                        int grid = (int)(((size_t)ctx->g.half * TS + block - 1) / block);
-                       // reducing launches: one wave of blocks keeps the partials (and the finishing
-                       // block's tail) short
-                       int cap = (EPI == EPI_AXPY && a.partials) ? ctx->num_sms * (2048 / block)
-                                                                : max_grid_blocks(ctx, block);
+                       // reducing launches: one wave of the blocks that are resident together keeps the
+                       // partials (and the finishing block's tail) short
+                       int cap = max_grid_blocks(ctx, block);
+                       if (EPI == EPI_AXPY && a.partials) {
+                         int per_sm = 0;
+                         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &per_sm, dslash_kernel<LR, SR, NR, EPI, COMP, TS>, block, 0);
+                         cap = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+                       }
                        if (grid > cap) grid = cap;
                        dslash_kernel<LR, SR, NR, EPI, COMP, TS><<<grid, block, 0, ctx->stream>>>(a);
                        return cudaGetLastError();

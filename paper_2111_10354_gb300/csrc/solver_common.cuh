@@ -63,6 +63,29 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NQ], double* partials, s
   return true;
 }
 
+// Reduce one quantity per grid row (y = rhs) over the row's x-blocks: the last block of a row to finish
+// sums that row's partials in block order, so the rows' tails overlap instead of queueing behind one
+// block. row_counters[gridDim.y] start at zero and are reset by each row's last block. Returns true
+// in every thread of that block; thread 0 then holds the row total in *total.
+__device__ __forceinline__ bool row_reduce(double v, double* partials, size_t pstride, unsigned* row_counters,
+                                           double* total) {
+  __shared__ double red[32];
+  __shared__ bool is_last;
+  const int r = blockIdx.y;
+  const double s = block_sum_dyn(v, red);
+  if (threadIdx.x == 0) partials[(size_t)r * pstride + blockIdx.x] = s;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(&row_counters[r], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  if (threadIdx.x == 0) row_counters[r] = 0u;
+  const double t = sum_partials_dyn(partials + (size_t)r * pstride, gridDim.x, red);
+  if (threadIdx.x == 0) *total = t;
+  return true;
+}
+
 template <typename S>
 struct SAcc {
   using T = typename Real<S>::acc;
