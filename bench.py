@@ -52,7 +52,7 @@ def parse():
                     help="time the steps only: no e2e, comparison solves or CPU baseline (for profiler launch lists)")
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
     ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-df64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8",
-                                                   "cg-f32-nr8", "ptc", "batch"],
+                                                   "cg-f32-nr8", "ptc", "fcg", "batch"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
@@ -738,6 +738,24 @@ def run_kernel_case(name):
             net.apply(z, r, 1)
         torch.cuda.synchronize()
         print(json.dumps({"case": name, "ok": True}))
+    elif name == "fcg":
+        # flexible CG with the (untrained, tied) PTC preconditioner: the launch mix of one solve
+        import oracle.ptc as optc
+        L = (32, 32, 32, 8)
+        fat, lng = hin.gen_links(L, 4100, 0.35, 0.1)
+        lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=stream).load(fat, lng)
+        net = h.Ptc(lat)
+        W1, _ = optc.init_weights(4000, scale=0.05)
+        net.set_tied(True)
+        net.set_weights(W1, optc.tie(W1))
+        b = torch.from_numpy(hin.gen_source(6000, lat.half, 1)).cuda()
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        for _ in range(2):
+            x.zero_()
+            torch.cuda.synchronize()
+            rc, st = h.hisq_fcg(lat.ctx, net.h, x, b, 0.001, 1e-10, 400, h.make_opts(), raise_on_error=False)
+        print(json.dumps({"case": name, "status": rc, "iters": st["iters"], "s": round(st["seconds"], 4)}))
     elif name == "batch":
         mix = hin.lattice_mix_64()[:16] + hin.lattice_mix_64()[32:40] + hin.lattice_mix_64()[51:55]
         batch = h.Batch([m["dims"] for m in mix], stream=stream)
