@@ -486,7 +486,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
                       "/" + std::to_string(cycle);
     char buf[64];
     for (const void* ptr : {(const void*)B.r, (const void*)B.p, (const void*)B.Ap, (const void*)B.t,
-                            (const void*)B.e, (const void*)B.st, (const void*)B.partials}) {
+                            (const void*)B.e, (const void*)B.st, (const void*)B.partials, (const void*)B.rowc}) {
       snprintf(buf, sizeof buf, "/%p", ptr);
       key += buf;
     }

@@ -230,7 +230,12 @@ __global__ void __launch_bounds__(256) k_ptc_forward(const PtcGeom G, const floa
         const int row = item % PTC_TILE, hl = item / PTC_TILE, h = h0 + hl;
         int c[4], idx, oi;
         cplx<float> u[CIN][3];
-        if (tile_site(g, OUT_EVEN, tile, row, c, &idx, &oi)) {
+        // layer 1 (CIN = 1) reads the network input, an even-site vector embedded with zeros on odd
+        // sites: the identity hop of an odd site and the +-mu hops of an even site transport zeros,
+        // so they load no link and no vector
+        bool live = tile_site(g, OUT_EVEN, tile, row, c, &idx, &oi);
+        if (CIN == 1 && live) live = (h == 0) == (((c[0] + c[1] + c[2] + c[3]) & 1) == 0);
+        if (live) {
           transport_multi<CIN>(G, in, c, idx, h, u);
         } else {
 #pragma unroll
