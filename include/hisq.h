@@ -327,9 +327,23 @@ double hisq_dslash_bytes(const hisq_ctx* ctx, int prec, int nrhs);
 long long hisq_launch_count(const hisq_ctx* ctx);
 
 /* Autotuner: choose launch shapes by timing (default on). The cache lives in the
- * context; hisq_tune_report writes "kernel dims prec nrhs -> block" lines to buf. */
+ * context; hisq_tune_report writes one "key LxxLyxLzxLt -> choice" line per tuned kernel to buf
+ * (choice = launch-form index * 10000 + block size). hisq_tune_load reads such a report back
+ * into a context of the same lattice dims (lines for other dims are skipped), so a later run can
+ * skip the timing launches; *loaded (may be NULL) receives the number of entries taken.
+ * Errors: HISQ_EINVAL (null context or text, malformed line). */
 int hisq_set_autotune(hisq_ctx* ctx, int enable);
 int hisq_tune_report(const hisq_ctx* ctx, char* buf, size_t len);
+int hisq_tune_load(hisq_ctx* ctx, const char* report, int* loaded);
+
+/*
+ * Self-test of the failure path of the bounded device-side waits (the completion waits of the
+ * tensor-core kernels give up after a bounded number of polls, flag the failure and return
+ * instead of hanging): launches one block that waits on an mbarrier nothing arrives at. Returns
+ * HISQ_ETIMEOUT when the wait gave up as intended -- the expected result -- after which the
+ * context remains usable. The paper has no counterpart.
+ */
+int hisq_selftest_bounded_wait(hisq_ctx* ctx);
 
 #ifdef __cplusplus
 }

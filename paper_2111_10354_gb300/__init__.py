@@ -99,6 +99,8 @@ def _load():
     lib.hisq_launch_count.argtypes = [vp]
     lib.hisq_launch_count.restype = ctypes.c_longlong
     lib.hisq_tune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.hisq_tune_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
+    lib.hisq_selftest_bounded_wait.argtypes = [vp]
     lib.hisq_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(ctypes.c_int), ctypes.c_uint, vp]
     lib.hisq_batch_destroy.argtypes = [vp]
     lib.hisq_batch_load_links.argtypes = [vp, ip, vp, vp, ctypes.c_uint]
@@ -282,6 +284,18 @@ def hisq_tune_report(ctx) -> str:
     buf = ctypes.create_string_buffer(1 << 16)
     _check(_load().hisq_tune_report(ctx, buf, len(buf)), "hisq_tune_report")
     return buf.value.decode()
+
+
+def hisq_tune_load(ctx, report: str) -> int:
+    """Load a tune report (from hisq_tune_report) into a context; returns the entries taken."""
+    n = ctypes.c_int(0)
+    _check(_load().hisq_tune_load(ctx, report.encode(), ctypes.byref(n)), "hisq_tune_load")
+    return n.value
+
+
+def hisq_selftest_bounded_wait(ctx) -> int:
+    """Status of the bounded-wait self-test (HISQ_ETIMEOUT when the wait gave up as intended)."""
+    return _load().hisq_selftest_bounded_wait(ctx)
 
 
 def hisq_batch_create(dims_list, prec_mask: int = HISQ_PREC_BIT(HISQ_F64) | HISQ_PREC_BIT(HISQ_F32), stream=None):

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include "internal.cuh"
+#include "trace.h"
 #include "tune.h"
 
 namespace hisq {
@@ -285,6 +286,7 @@ int hisq_destroy(hisq_ctx* c) {
 
 int hisq_load_links_slab(hisq_ctx* c, int t_begin, int t_count, const double* fat, const double* lng,
                          unsigned flags) {
+  TraceRange trace("hisq_load_links_slab");
   if (!c || !fat || !lng) return set_error(HISQ_EINVAL, "null argument");
   if (t_begin < 0 || t_count < 1 || t_begin + t_count > c->g.L[3])
     return set_error(HISQ_EINVAL, "t-slab [%d, %d) outside [0, %d)", t_begin, t_begin + t_count, c->g.L[3]);
@@ -464,13 +466,39 @@ int hisq_set_autotune(hisq_ctx* c, int enable) {
   return HISQ_OK;
 }
 
+int hisq_tune_load(hisq_ctx* c, const char* report, int* loaded) {
+  if (!c || !report) return set_error(HISQ_EINVAL, "null argument");
+  int n = 0;
+  const char* line = report;
+  while (*line) {
+    const char* end = strchr(line, '\n');
+    const size_t len = end ? (size_t)(end - line) : strlen(line);
+    if (len > 0) {
+      char key[128];
+      int L[4], value;
+      const std::string text(line, len);
+      if (sscanf(text.c_str(), "%127s %dx%dx%dx%d -> %d", key, &L[0], &L[1], &L[2], &L[3], &value) != 6 ||
+          value < 1)
+        return set_error(HISQ_EINVAL, "malformed tune line: %.80s", text.c_str());
+      if (L[0] == c->g.L[0] && L[1] == c->g.L[1] && L[2] == c->g.L[2] && L[3] == c->g.L[3]) {
+        c->tune[key] = -value;  // checked against the kernel's launch forms at first use
+        ++n;
+      }
+    }
+    if (!end) break;
+    line = end + 1;
+  }
+  if (loaded) *loaded = n;
+  return HISQ_OK;
+}
+
 int hisq_tune_report(const hisq_ctx* c, char* buf, size_t len) {
   if (!c || !buf || len == 0) return set_error(HISQ_EINVAL, "null argument");
   size_t used = 0;
   buf[0] = 0;
   for (auto& kv : c->tune) {
     int n = snprintf(buf + used, len - used, "%s %dx%dx%dx%d -> %d\n", kv.first.c_str(), c->g.L[0], c->g.L[1],
-                     c->g.L[2], c->g.L[3], kv.second);
+                     c->g.L[2], c->g.L[3], kv.second < 0 ? -kv.second : kv.second);
     if (n < 0 || (size_t)n >= len - used) break;
     used += n;
   }

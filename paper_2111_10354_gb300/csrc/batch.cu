@@ -18,6 +18,7 @@
 
 #include "dslash_impl.cuh"
 #include "solver_common.cuh"
+#include "trace.h"
 #include "tune.h"
 
 namespace hisq {
@@ -804,6 +805,7 @@ long long hisq_batch_launch_count(const hisq_batch* B) { return B ? B->launches 
 
 int hisq_batch_cg(hisq_batch* B, double* x, const double* b, const double* mass, double rel_tol, int maxiter,
                   const hisq_solver_opts* opts, hisq_solver_stats* stats, int* iters, double* true_res) {
+  TraceRange trace("hisq_batch_cg");
   if (!B || !x || !b || !mass) return set_error(HISQ_EINVAL, "null argument");
   for (int l = 0; l < B->nlat; ++l) {
     if (!B->lat[l]->links_ready) return set_error(HISQ_ENOLINKS, "lattice %d has no links", l);

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "solver_common.cuh"
+#include "trace.h"
 #include "tune.h"
 
 namespace hisq {
@@ -519,6 +520,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
       c2.counter = ctx->d_counters + 3;
       if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
 
+      TraceRange trace("cg graph capture");
       cudaGraph_t graph;
       HISQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
       ctx->capturing = true;
@@ -585,6 +587,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
     bool all_inner = true;
     for (int q = 0; q < nrhs; ++q) all_inner = all_inner && hst->rhs_done[q];
     if (mixed || all_inner) {
+      TraceRange trace("reliable update");
       if ((rc = fold()) != HISQ_OK) return rc;
       if ((rc = true_residual(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
       if ((rc = reliable<S>(ctx, B, nrhs, 0)) != HISQ_OK) return rc;
@@ -1074,6 +1077,7 @@ static int unstage(hisq_ctx* ctx, double* x, size_t xb, const Staged& s, int rc)
 
 int hisq_cg(hisq_ctx* ctx, double* x, const double* b, int nrhs, double mass, double rel_tol, int maxiter,
             const hisq_solver_opts* opts, hisq_solver_stats* stats) {
+  TraceRange trace("hisq_cg");
   hisq_solver_opts o;
   int rc = check_solver(ctx, x, b, mass, maxiter, opts, &o);
   if (rc != HISQ_OK) return rc;
@@ -1095,6 +1099,7 @@ int hisq_cg(hisq_ctx* ctx, double* x, const double* b, int nrhs, double mass, do
 
 int hisq_multishift_cg(hisq_ctx* ctx, double* x, const double* b, int nshift, const double* shifts, double mass,
                        const double* rel_tol, int maxiter, const hisq_solver_opts* opts, hisq_solver_stats* stats) {
+  TraceRange trace("hisq_multishift_cg");
   hisq_solver_opts o;
   int rc = check_solver(ctx, x, b, mass, maxiter, opts, &o);
   if (rc != HISQ_OK) return rc;

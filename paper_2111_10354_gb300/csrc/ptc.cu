@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "trace.h"
 #include "tc.cuh"
 
 namespace hisq {
@@ -1135,6 +1136,7 @@ int hisq_ptc_apply(hisq_ptc* P, float* z, const float* r, int nvec) {
 // even-site FP32 (b, x) pairs; with lr > 0 an Adam step follows. g1, g2, loss: optional host outputs.
 int hisq_ptc_train_step(hisq_ptc* P, const float* b, const float* x, int npairs, float lr, float* loss_out,
                         float* g1_out, float* g2_out) {
+  TraceRange trace("hisq_ptc_train_step");
   if (!P || !b || !x || npairs < 1) return set_error(HISQ_EINVAL, "bad argument");
   if (!P->ctx->links_ready) return set_error(HISQ_ENOLINKS, "links not loaded");
   if (!is_device_ptr(b) || !is_device_ptr(x)) return set_error(HISQ_EINVAL, "device vectors only");
@@ -1221,6 +1223,7 @@ int hisq_ptc_train_step(hisq_ptc* P, const float* b, const float* x, int npairs,
 
 int hisq_fcg(hisq_ctx* c, hisq_ptc* P, double* x_user, const double* b_user, double mass, double rel_tol,
              int maxiter, const hisq_solver_opts* opts, hisq_solver_stats* stats) {
+  TraceRange trace("hisq_fcg");
   if (!c || !P || !x_user || !b_user) return set_error(HISQ_EINVAL, "null argument");
   if (P->ctx != c) return set_error(HISQ_EINVAL, "the network belongs to another context");
   if (!c->links_ready) return set_error(HISQ_ENOLINKS, "links not loaded");

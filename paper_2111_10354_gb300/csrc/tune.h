@@ -28,10 +28,25 @@ struct TuneVariant {
 // variant * 10000 + block. With one variant this is a plain block-size tuner.
 inline int tuned_variant(hisq_ctx* ctx, const char* key, const TuneVariant* v, int nv, int* vi_out, int* block_out) {
   auto it = ctx->tune.find(key);
-  if (it != ctx->tune.end()) {
+  if (it != ctx->tune.end() && it->second > 0) {
     *vi_out = it->second / 10000;
     *block_out = it->second % 10000;
     return HISQ_OK;
+  }
+  if (it != ctx->tune.end()) {
+    // a choice loaded from a report (stored negated until checked) is kept only if it names an
+    // existing form and a block size that form can launch; otherwise the key is tuned again
+    const int vi = -it->second / 10000, b = -it->second % 10000;
+    cudaFuncAttributes fa;
+    if (vi < nv && (b == 64 || b == 128 || b == 256 || b == 512) &&
+        cudaFuncGetAttributes(&fa, v[vi].func) == cudaSuccess && b <= fa.maxThreadsPerBlock) {
+      it->second = -it->second;
+      *vi_out = vi;
+      *block_out = b;
+      return HISQ_OK;
+    }
+    cudaGetLastError();
+    ctx->tune.erase(it);
   }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   HISQ_CUDA(cudaStreamIsCapturing(ctx->stream, &cap));
