@@ -474,6 +474,11 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
     if (!isfinite(hst->bb[q]) || !isfinite(hst->rr_true[q]))
       return set_error(HISQ_ENONFINITE, "non-finite source or initial guess (rhs %d)", q);
     hst->tol2[q] = tol[q] * tol[q] * hst->bb[q];
+    if (hst->bb[q] == 0.0) {
+      // a zero source has the exact solution x = 0 (its relative residual is not defined)
+      HISQ_CUDA(cudaMemsetAsync(x + (size_t)q * n, 0, n * sizeof(double2), ctx->stream));
+      hst->rr_true[q] = 0.0;
+    }
   }
   HISQ_CUDA(cudaMemcpyAsync(B.st, hst, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
   if ((rc = reliable<S>(ctx, B, nrhs, 1)) != HISQ_OK) return rc;

@@ -38,7 +38,7 @@ inline int tuned_variant(hisq_ctx* ctx, const char* key, const TuneVariant* v, i
     // existing form and a block size that form can launch; otherwise the key is tuned again
     const int vi = -it->second / 10000, b = -it->second % 10000;
     cudaFuncAttributes fa;
-    if (vi < nv && (b == 64 || b == 128 || b == 256 || b == 512) &&
+    if (vi < nv && b >= 32 && b % 32 == 0 &&
         cudaFuncGetAttributes(&fa, v[vi].func) == cudaSuccess && b <= fa.maxThreadsPerBlock) {
       it->second = -it->second;
       *vi_out = vi;
@@ -59,7 +59,9 @@ inline int tuned_variant(hisq_ctx* ctx, const char* key, const TuneVariant* v, i
     if (cap == cudaStreamCaptureStatusNone) ctx->tune[key] = b;
     return HISQ_OK;
   }
-  static const int cands[] = {64, 128, 256, 512};
+  // powers of two and the sizes between them: on small lattices a block size that spreads the
+  // blocks evenly over the SMs matters
+  static const int cands[] = {64, 96, 128, 160, 192, 224, 256, 384, 512};
   cudaEvent_t e0, e1;
   HISQ_CUDA(cudaEventCreate(&e0));
   HISQ_CUDA(cudaEventCreate(&e1));

@@ -138,3 +138,23 @@ def test_cg_repeated_solves_reuse_graphs(hisq):
         xs.append(x.cpu())
     assert torch.equal(xs[0], xs[2])
     assert not torch.equal(xs[0], xs[1])
+
+
+def test_cg_zero_source_and_max_rhs(hisq):
+    """Degenerate and maximal cases: a zero source returns x = 0 at once; 64 right-hand sides (the
+    maximum) in one mixed solve, every one to its true residual."""
+    import torch
+    L = (4, 6, 8, 10)
+    lat, ff, lf = lattice(hisq, L, 51, precs=(0, 1))
+    z = torch.zeros((1, lat.half, 3), dtype=torch.complex128, device="cuda")
+    x = torch.ones_like(z)
+    rc, st = lat.cg(x, z, 0.1, 1e-10, 100, inner_prec=1)
+    assert rc == 0 and st["converged"] == 1 and st["iters"] == 0
+    assert float(torch.linalg.vector_norm(x)) == 0.0 and st["true_rel_residual"] == 0.0
+    b = hin.gen_source(52, lat.half, 64)
+    x = torch.zeros((64, lat.half, 3), dtype=torch.complex128, device="cuda")
+    rc, st = lat.cg(x, torch.from_numpy(b).cuda(), 0.1, 1e-10, 2000, nrhs=64, inner_prec=1)
+    assert rc == 0
+    xs = x.cpu().numpy()
+    for r in (0, 17, 63):
+        assert oracle.true_residual(L, ff, lf, 0.1, b[r], xs[r]) <= 1e-10

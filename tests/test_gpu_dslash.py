@@ -4,7 +4,8 @@ Tolerance (relative global L2 over the whole output): FP64 1e-12, FP32 2e-6, FP1
 double-float precision (prec 4: FP64 vectors, links as FP32 pairs, 2^-47 rounding per operation) is held
 to the FP64 tolerance.
 Lattices: 8^4 (the plain-method workload), 8x10x12x14 (every hop distinct, ragged last block),
-4x6x8x10 (hops alias and must accumulate), 16^3x8 (several tiles).
+4x6x8x10 (hops alias and must accumulate), 16^3x8 (several tiles), 4^4 (the smallest lattice: the +3 and -1
+hops coincide in every direction).
 """
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-12, 1: 2e-6, 2: 5e-3, 3: 5e-3, 4: 1e-12}
 F64_LAYOUT = (0, 4)  # precisions whose boundary vectors are complex128
-LATTICES = [(8, 8, 8, 8), (8, 10, 12, 14), (4, 6, 8, 10), (16, 16, 16, 8)]
+LATTICES = [(8, 8, 8, 8), (8, 10, 12, 14), (4, 6, 8, 10), (16, 16, 16, 8), (4, 4, 4, 4)]
 
 
 def to_device(vec, prec):
