@@ -218,3 +218,38 @@ def test_slab_loading_matches_whole(hisq):
     whole.dslash(0, y1, x, 0)
     slab.dslash(0, y2, x, 0)
     assert torch.equal(y1, y2)
+
+
+# launch forms per rhs group (vectors per thread x threads per site), in the tuner's variant order;
+# 8-vector groups exist below FP64 only
+FORMS = {1: 1, 2: 2, 4: 3, 8: 3}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
+def test_every_launch_form_matches_oracle(hisq, prec):
+    """Each launch form the tuner can pick, forced through a loaded tune entry, against the oracle: the
+    Dslash (plain epilogue) and A (fused axpy epilogue) for groups of 1, 2, 4 and 8 vectors."""
+    L = (8, 10, 12, 14)
+    lat, ff, lf = setup(hisq, L)
+    half = lat.half
+    sp = 0 if prec == 4 else prec  # the double-float operator takes FP64 vectors
+    dims = "%dx%dx%dx%d" % L
+    for nr, nforms in FORMS.items():
+        if nr == 8 and prec in (0, 4):
+            continue
+        src = hin.gen_source(7000 + nr, half, nr)
+        x = to_device(src, prec)
+        for vi in range(nforms):
+            for epi in (0, 1):
+                key = "dslash/l%d/s%d/nr%d/e%d/c0" % (prec, sp, nr, epi)
+                assert hisq.hisq_tune_load(lat.ctx, "%s %s -> %d\n" % (key, dims, vi * 10000 + 96)) == 1
+            y = empty_like_prec((nr, half, 3), prec)
+            lat.dslash(0, y, x, prec, nr)
+            got = from_device(y, prec)
+            for r in range(nr):
+                assert rel_err(got[r], oracle.dslash(L, ff, lf, 0, src[r])) <= TOL[prec], (prec, nr, vi, r)
+            lat.apply_A(y, x, 0.05, prec, nr)
+            got = from_device(y, prec)
+            for r in range(nr):
+                ref = oracle.apply_A(L, ff, lf, 0.05, src[r])
+                assert rel_err(got[r], ref) <= 2 * TOL[prec], (prec, nr, vi, r)
