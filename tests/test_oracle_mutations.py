@@ -37,14 +37,14 @@ def scratch(tmp_path_factory):
         shutil.copytree(os.path.join(ROOT, sub), os.path.join(d, sub),
                         ignore=shutil.ignore_patterns("liboracle.so", "__pycache__", "*.tmp*"))
     os.makedirs(os.path.join(d, "tests"))
-    for f in ("conftest.py", "test_oracle_dslash.py", "test_oracle_solvers.py"):
+    for f in ("conftest.py", "test_oracle_dslash.py", "test_oracle_solvers.py", "test_oracle_smear.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(d, "tests", f))
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(d, "tests", "golden"))
     return str(d)
 
 
-def run_pins(d):
-    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "tests"], cwd=d,
+def run_pins(d, target="tests"):
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", target], cwd=d,
                          capture_output=True, text=True, timeout=600)
     return res.returncode, res.stdout[-400:]
 
@@ -72,3 +72,33 @@ def test_mutation_is_caught(scratch, name, old, new):
             f.write(original)
         if os.path.exists(lib):
             os.remove(lib)
+
+
+SMEAR_MUTATIONS = [
+    ("backward step without the dagger", "M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))", "M = M @ U[at, d]"),
+    ("backward step takes the link at the starting site",
+     "at = _shift_index(L, d, -1)[at]\n            M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))",
+     "M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))\n            at = _shift_index(L, d, -1)[at]"),
+    ("five-link staple closed in crossed order", "(mu, 1), (nu, -s), (rho, -r)]", "(mu, 1), (rho, -r), (nu, -s)]"),
+    ("seven-link staple returning on the wrong side", "(rho, -r), (sigma, -q)]", "(rho, -r), (sigma, q)]"),
+    ("Lepage term displaced one site only", "paths[\"lepage\"].append([(nu, s), (nu, s), (mu, 1), (nu, -s), (nu, -s)])",
+     "paths[\"lepage\"].append([(nu, s), (mu, 1), (nu, -s)])"),
+    ("Naik link of two hops", "[(mu, 1), (mu, 1), (mu, 1)]", "[(mu, 1), (mu, 1)]"),
+    ("projection by (W^dag W)^(1/2)", "(1.0 / np.sqrt(lam))", "np.sqrt(lam)"),
+    ("projection factor on the wrong side", "return W @ inv_sqrt", "return inv_sqrt @ W"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", SMEAR_MUTATIONS, ids=[m[0] for m in SMEAR_MUTATIONS])
+def test_smear_mutation_is_caught(scratch, name, old, new):
+    src_path = os.path.join(scratch, "oracle", "smear.py")
+    original = open(os.path.join(ROOT, "oracle", "smear.py")).read()
+    assert old in original, "mutation anchor missing: " + old
+    with open(src_path, "w") as f:
+        f.write(original.replace(old, new, 1))
+    try:
+        rc, out = run_pins(scratch, "tests/test_oracle_smear.py")
+        assert rc != 0, "pins did not catch: " + name
+    finally:
+        with open(src_path, "w") as f:
+            f.write(original)
