@@ -39,6 +39,7 @@ MASS = 0.01
 TOL = 1e-10
 GAUGE_SEED, SOURCE_SEED = 1001, 2001
 FALLBACK_HBM = 6800.0
+FP64_PIPE_TFLOPS = 1.20  # GB300 DFMA throughput, measured on this GPU type with an independent-FMA loop
 
 
 def parse():
@@ -52,9 +53,9 @@ def parse():
                     help="time the steps only: no e2e, comparison solves or CPU baseline (for profiler launch lists)")
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
     ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-df64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8",
-                                                   "cg-f32-nr8", "ptc", "fcg", "batch"],
+                                                   "cg-f32-nr8", "ptc", "fcg", "batch", "smear-f64", "smear-df64"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
-    ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned"],
+    ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned", "smear"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
     return ap.parse_args()
 
@@ -677,6 +678,67 @@ def row_learned(h, torch, hin, epochs=6, batch_pairs=16):
                                       "true_res": st_d["true_rel_residual"]}}), flush=True)
 
 
+SMEAR_LEVEL1 = dict(c1=1 / 8, c3=1 / 16, c5=1 / 64, c7=1 / 384)  # fat7
+SMEAR_LEVEL2 = dict(c1=5 / 8, c3=1 / 16, c5=1 / 64, c7=1 / 384, cL=-1 / 16, cN=-1 / 24)  # asqtad-type
+# one smearing level: 50 products of 3x3 complex matrices per site and direction (27 complex
+# multiply-adds = 216 flops each); linear combinations are not counted
+SMEAR_FLOPS_PER_SITE = 4 * 50 * 216
+
+
+def _stream_ms(torch, stream, fn, reps):
+    fn()  # workspaces
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def row_smear(h, torch, hin):
+    """48^3x12 link smearing: one level with every path kind and the Naik product in FP64 and in
+    double-float arithmetic, the U(3) projection, the two HISQ levels, and the oracle on sampled sites."""
+    from oracle import smear as sm
+    L = (48, 48, 48, 12)
+    V = int(np.prod(L))
+    Uh = hin.gen_thin(L, GAUGE_SEED, 0.3).reshape(V, 4, 3, 3)
+    stream = torch.cuda.Stream()
+    lat = h.Lattice(L, precs=(h.HISQ_F64,), stream=stream)
+    U = torch.from_numpy(Uh).cuda()
+    fat, lng = torch.empty_like(U), torch.empty_like(U)
+    torch.cuda.synchronize()
+    lname = "x".join(map(str, L))
+    gpu_sites = {}
+    for prec, name in ((h.HISQ_F64, "f64"), (h.HISQ_DF64, "df64")):
+        ms = _stream_ms(torch, stream, lambda: lat.smear(fat, lng, U, SMEAR_LEVEL2, prec), 3)
+        gf = SMEAR_FLOPS_PER_SITE * V / (ms * 1e-3) / 1e9
+        line = {"row": "smear", "lattice": lname, "arith": name, "what": "one level, all paths + Naik",
+                "ms": round(ms, 3), "GFLOP/s": round(gf, 1), "sites_per_s": round(V / (ms * 1e-3), 1)}
+        if prec == h.HISQ_F64:
+            line["frac_fp64_pipe"] = round(gf / (FP64_PIPE_TFLOPS * 1e3), 3)
+        gpu_sites[name] = V / (ms * 1e-3)
+        print(json.dumps(line), flush=True)
+        ms = _stream_ms(torch, stream, lambda: lat.hisq_links(fat, lng, U, SMEAR_LEVEL1, SMEAR_LEVEL2, prec), 3)
+        print(json.dumps({"row": "smear", "lattice": lname, "arith": name,
+                          "what": "two HISQ levels (level 1, U(3) projection, level 2 + Naik)",
+                          "ms": round(ms, 3)}), flush=True)
+    ms = _stream_ms(torch, stream, lambda: h.hisq_project_u3(lat.ctx, fat, U), 5)
+    by = 2 * V * 4 * 144
+    print(json.dumps({"row": "smear", "lattice": lname, "what": "U(3) projection (FP64)", "ms": round(ms, 3),
+                      "GB/s": round(by / (ms * 1e-3) / 1e9, 1)}), flush=True)
+    # the oracle (numpy, explicit path sums) on a sample of sites
+    n = 2048
+    sample = np.random.default_rng(3).choice(V, n, replace=False)
+    t0 = time.perf_counter()
+    sm.smear(L, Uh, **SMEAR_LEVEL2, sites=sample)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"row": "smear", "lattice": lname, "what": "oracle, one level on %d sampled sites" % n,
+                      "s": round(dt, 3), "sites_per_s": round(n / dt, 1),
+                      "gpu_over_oracle": {k: round(v / (n / dt), 1) for k, v in gpu_sites.items()}}), flush=True)
+
+
 def run_row(name):
     import torch
 
@@ -685,7 +747,7 @@ def run_row(name):
     __graft_entry__.build()
     import paper_2111_10354_gb300 as h
     {"multirhs": row_multirhs, "multishift": row_multishift, "batch": row_batch,
-     "learned": row_learned}[name](h, torch, hin)
+     "learned": row_learned, "smear": row_smear}[name](h, torch, hin)
 
 
 def run_kernel_case(name):
@@ -756,6 +818,16 @@ def run_kernel_case(name):
             torch.cuda.synchronize()
             rc, st = h.hisq_fcg(lat.ctx, net.h, x, b, 0.001, 1e-10, 400, h.make_opts(), raise_on_error=False)
         print(json.dumps({"case": name, "status": rc, "iters": st["iters"], "s": round(st["seconds"], 4)}))
+    elif name.startswith("smear"):
+        L = (32, 32, 32, 8)
+        V = int(np.prod(L))
+        lat = h.Lattice(L, precs=(h.HISQ_F64,), stream=stream)
+        U = torch.from_numpy(hin.gen_thin(L, GAUGE_SEED, 0.3).reshape(V, 4, 3, 3)).cuda()
+        fat, lng = torch.empty_like(U), torch.empty_like(U)
+        torch.cuda.synchronize()
+        prec = h.HISQ_DF64 if name == "smear-df64" else h.HISQ_F64
+        ms = _stream_ms(torch, stream, lambda: lat.smear(fat, lng, U, SMEAR_LEVEL2, prec), 1)
+        print(json.dumps({"case": name, "ms": round(ms, 3)}))
     elif name == "batch":
         mix = hin.lattice_mix_64()[:16] + hin.lattice_mix_64()[32:40] + hin.lattice_mix_64()[51:55]
         batch = h.Batch([m["dims"] for m in mix], stream=stream)

@@ -314,6 +314,53 @@ int hisq_rational_apply(hisq_ctx* ctx, double* out, const double* b, double a0, 
                         const double* coeffs, double mass, const double* rel_tol, int maxiter,
                         const hisq_solver_opts* opts, hisq_solver_stats* stats);
 
+/* ---------------------------------------------------------------- link smearing */
+/*
+ * Path coefficients of one smearing level of HISQ type (the HISQ action of the paper's simulations,
+ * Sec. 1, builds its fat and long links this way; the coefficients are not in the paper and are the
+ * caller's). For every site x and direction mu, with paths read as products of the links walked
+ * (U_d(y) for a step +d from y, U_d(y-d)^dag for a step -d):
+ *   fat_mu(x)  = one_link U_mu(x)
+ *              + three_staple * sum of the  6 paths (nu, mu, -nu)                 nu != mu, both signs
+ *              + five_staple  * sum of the 24 paths (rho, nu, mu, -nu, -rho)      nu, rho, mu distinct
+ *              + seven_staple * sum of the 48 paths (sig, rho, nu, mu, -nu, -rho, -sig)  all distinct
+ *              + lepage       * sum of the  6 paths (nu, nu, mu, -nu, -nu)
+ *   long_mu(x) = naik U_mu(x) U_mu(x+mu) U_mu(x+2mu)
+ * The staggered phases and the boundary sign are not applied (hisq_load_links folds them in).
+ */
+typedef struct {
+  double one_link, three_staple, five_staple, seven_staple, lepage, naik;
+} hisq_smear_coeffs;
+
+/*
+ * One smearing level on the device. thin: input links; fat, lng: outputs; all three device
+ * pointers (16-byte aligned) in the link layout of hisq_load_links (V*4*9 complex128, so the
+ * outputs can be passed to hisq_load_links directly). lng may be NULL (long links not formed).
+ * Outputs must not overlap the input or each other. prec: the arithmetic, HISQ_F64 (IEEE FP64) or
+ * HISQ_DF64 (double-float on the FP32 pipe, ~2^-47 relative rounding per operation); inputs and
+ * outputs are binary64 either way. Uses 117 * 16 bytes of context workspace per site. Stream-ordered,
+ * no host synchronisation. Errors: HISQ_EINVAL (null or host pointer, misaligned, overlapping,
+ * non-finite coefficient, other prec), HISQ_ENOMEM, HISQ_ECUDA.
+ */
+int hisq_smear(hisq_ctx* ctx, double* fat, double* lng, const double* thin, const hisq_smear_coeffs* c, int prec);
+
+/*
+ * Projection of every link onto U(3): out = W (W^dag W)^{-1/2} for each 3x3 link W of in (device
+ * pointers, link layout; out == in is allowed, partial overlap is not). FP64. Synchronises the
+ * stream. Returns HISQ_EINVAL if some W^dag W is not positive definite (that link is copied
+ * unchanged).
+ */
+int hisq_project_u3(hisq_ctx* ctx, double* out, const double* in);
+
+/*
+ * The two levels of the HISQ construction: W = project_u3(level-1 fat links of thin), then the
+ * level-2 fat links of W into fat and the Naik product of W into lng (level1's naik is unused).
+ * Arguments and errors as hisq_smear and hisq_project_u3 (synchronises the stream); also uses
+ * V*4*9 complex128 of workspace for W.
+ */
+int hisq_hisq_links(hisq_ctx* ctx, double* fat, double* lng, const double* thin, const hisq_smear_coeffs* level1,
+                    const hisq_smear_coeffs* level2, int prec);
+
 /* ---------------------------------------------------------------- diagnostics */
 const char* hisq_strerror(int code);
 const char* hisq_last_error(void);

@@ -30,26 +30,24 @@ import numpy as np
 from . import coords, volume
 
 
-def _shift_index(L, d: int, k: int):
-    """Lexicographic index of x + k*d-hat for every site x."""
-    idx = np.arange(volume(L))
+def _shift_index(L, d: int, k: int, idx):
+    """Lexicographic index of x + k*d-hat for the sites x with lexicographic indices idx."""
     c = list(coords(L, idx))
     c[d] = (c[d] + k) % L[d]
     return c[0] + L[0] * (c[1] + L[1] * (c[2] + L[2] * c[3]))
 
 
-def path_product(L, U, steps):
-    """Product of the links along `steps` (list of (direction, +1/-1)) starting at every site.
-    U: (V, 4, 3, 3) complex. Returns (V, 3, 3)."""
-    V = volume(L)
-    at = np.arange(V)  # current site of the walk, per starting site
-    M = np.broadcast_to(np.eye(3, dtype=np.complex128), (V, 3, 3)).copy()
+def path_product(L, U, steps, sites=None):
+    """Product of the links along `steps` (list of (direction, +1/-1)) starting at every site (or at
+    the lexicographic indices `sites`). U: (V, 4, 3, 3) complex. Returns (n, 3, 3)."""
+    at = np.arange(volume(L)) if sites is None else np.asarray(sites)  # current site of each walk
+    M = np.broadcast_to(np.eye(3, dtype=np.complex128), (len(at), 3, 3)).copy()
     for d, s in steps:
         if s > 0:
             M = M @ U[at, d]
-            at = _shift_index(L, d, +1)[at]
+            at = _shift_index(L, d, +1, at)
         else:
-            at = _shift_index(L, d, -1)[at]
+            at = _shift_index(L, d, -1, at)
             M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))
     return M
 
@@ -71,20 +69,22 @@ def staple_paths(mu: int):
     return paths
 
 
-def smear(L, U, c1=0.0, c3=0.0, c5=0.0, c7=0.0, cL=0.0, cN=0.0):
-    """One smearing level. U: (V, 4, 3, 3) complex128. Returns (fat, long), each (V, 4, 3, 3)."""
+def smear(L, U, c1=0.0, c3=0.0, c5=0.0, c7=0.0, cL=0.0, cN=0.0, sites=None):
+    """One smearing level. U: (V, 4, 3, 3) complex128. Returns (fat, long), each (V, 4, 3, 3), or
+    (len(sites), 4, 3, 3) for the links of the given sites only."""
     U = np.ascontiguousarray(U, dtype=np.complex128)
-    F = c1 * U.copy()
-    Lg = np.zeros_like(U)
+    sel = np.arange(volume(L)) if sites is None else np.asarray(sites)
+    F = c1 * U[sel].copy()
+    Lg = np.zeros_like(F)
     for mu in range(4):
         paths = staple_paths(mu)
         for kind, coef in (("three", c3), ("five", c5), ("seven", c7), ("lepage", cL)):
             if coef == 0.0:
                 continue
             for steps in paths[kind]:
-                F[:, mu] += coef * path_product(L, U, steps)
+                F[:, mu] += coef * path_product(L, U, steps, sel)
         if cN != 0.0:
-            Lg[:, mu] = cN * path_product(L, U, [(mu, 1), (mu, 1), (mu, 1)])
+            Lg[:, mu] = cN * path_product(L, U, [(mu, 1), (mu, 1), (mu, 1)], sel)
     return F, Lg
 
 

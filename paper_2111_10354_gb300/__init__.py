@@ -56,6 +56,16 @@ class hisq_solver_stats(ctypes.Structure):
         return d
 
 
+class hisq_smear_coeffs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("one_link", "three_staple", "five_staple", "seven_staple", "lepage",
+                                                "naik")]
+
+
+def smear_coeffs(c1=0.0, c3=0.0, c5=0.0, c7=0.0, cL=0.0, cN=0.0) -> hisq_smear_coeffs:
+    """Path coefficients of one smearing level: one link, 3-, 5-, 7-link staples, Lepage, Naik."""
+    return hisq_smear_coeffs(c1, c3, c5, c7, cL, cN)
+
+
 class HisqError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str, stats=None):
         self.code = code
@@ -101,6 +111,10 @@ def _load():
     lib.hisq_tune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.hisq_tune_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
     lib.hisq_selftest_bounded_wait.argtypes = [vp]
+    cp = ctypes.POINTER(hisq_smear_coeffs)
+    lib.hisq_smear.argtypes = [vp, vp, vp, vp, cp, ip]
+    lib.hisq_project_u3.argtypes = [vp, vp, vp]
+    lib.hisq_hisq_links.argtypes = [vp, vp, vp, vp, cp, cp, ip]
     lib.hisq_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(ctypes.c_int), ctypes.c_uint, vp]
     lib.hisq_batch_destroy.argtypes = [vp]
     lib.hisq_batch_load_links.argtypes = [vp, ip, vp, vp, ctypes.c_uint]
@@ -291,6 +305,27 @@ def hisq_tune_load(ctx, report: str) -> int:
     n = ctypes.c_int(0)
     _check(_load().hisq_tune_load(ctx, report.encode(), ctypes.byref(n)), "hisq_tune_load")
     return n.value
+
+
+def _coeffs(c):
+    return c if isinstance(c, hisq_smear_coeffs) else smear_coeffs(**c)
+
+
+def hisq_smear(ctx, fat, lng, thin, coeffs, prec: int = HISQ_F64):
+    """One smearing level on the device (fat, lng, thin: device arrays in the link layout; lng may be
+    None). coeffs: hisq_smear_coeffs or a dict of smear_coeffs' keywords."""
+    c = _coeffs(coeffs)
+    _check(_load().hisq_smear(ctx, _ptr(fat), _ptr(lng), _ptr(thin), ctypes.byref(c), prec), "hisq_smear")
+
+
+def hisq_project_u3(ctx, out, in_):
+    _check(_load().hisq_project_u3(ctx, _ptr(out), _ptr(in_)), "hisq_project_u3")
+
+
+def hisq_hisq_links(ctx, fat, lng, thin, level1, level2, prec: int = HISQ_F64):
+    c1, c2 = _coeffs(level1), _coeffs(level2)
+    _check(_load().hisq_hisq_links(ctx, _ptr(fat), _ptr(lng), _ptr(thin), ctypes.byref(c1), ctypes.byref(c2), prec),
+           "hisq_hisq_links")
 
 
 def hisq_selftest_bounded_wait(ctx) -> int:
@@ -505,6 +540,12 @@ class Lattice:
 
     def dslash(self, out_parity, out, in_, prec, nrhs=1):
         hisq_dslash(self.ctx, out_parity, out, in_, prec, nrhs)
+
+    def smear(self, fat, lng, thin, coeffs, prec=HISQ_F64):
+        hisq_smear(self.ctx, fat, lng, thin, coeffs, prec)
+
+    def hisq_links(self, fat, lng, thin, level1, level2, prec=HISQ_F64):
+        hisq_hisq_links(self.ctx, fat, lng, thin, level1, level2, prec)
 
     def apply_A(self, out, in_, mass, prec, nrhs=1, sigma=0.0):
         hisq_apply_A(self.ctx, out, in_, mass, sigma, prec, nrhs)

@@ -77,8 +77,8 @@ def test_mutation_is_caught(scratch, name, old, new):
 SMEAR_MUTATIONS = [
     ("backward step without the dagger", "M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))", "M = M @ U[at, d]"),
     ("backward step takes the link at the starting site",
-     "at = _shift_index(L, d, -1)[at]\n            M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))",
-     "M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))\n            at = _shift_index(L, d, -1)[at]"),
+     "at = _shift_index(L, d, -1, at)\n            M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))",
+     "M = M @ np.conj(np.swapaxes(U[at, d], -1, -2))\n            at = _shift_index(L, d, -1, at)"),
     ("five-link staple closed in crossed order", "(mu, 1), (nu, -s), (rho, -r)]", "(mu, 1), (rho, -r), (nu, -s)]"),
     ("seven-link staple returning on the wrong side", "(rho, -r), (sigma, -q)]", "(rho, -r), (sigma, q)]"),
     ("Lepage term displaced one site only", "paths[\"lepage\"].append([(nu, s), (nu, s), (mu, 1), (nu, -s), (nu, -s)])",
