@@ -196,16 +196,25 @@ def hisq_destroy(ctx):
     _check(_load().hisq_destroy(ctx), "hisq_destroy")
 
 
+def _links_arg(a):
+    """Links as passed to the library: a complex128 torch tensor (host or device) as is, anything
+    else as a contiguous complex128 numpy array."""
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != "torch.complex128":
+            raise TypeError("links must be complex128, got %s" % a.dtype)
+        return a
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
 def hisq_load_links(ctx, fat, lng, flags: int = HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T):
-    fat = np.ascontiguousarray(fat, dtype=np.complex128)
-    lng = np.ascontiguousarray(lng, dtype=np.complex128)
+    """fat, lng: host or device arrays in the link layout (complex128)."""
+    fat, lng = _links_arg(fat), _links_arg(lng)
     _check(_load().hisq_load_links(ctx, _ptr(fat), _ptr(lng), flags), "hisq_load_links")
 
 
 def hisq_load_links_slab(ctx, t_begin: int, t_count: int, fat, lng,
                          flags: int = HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T):
-    fat = np.ascontiguousarray(fat, dtype=np.complex128)
-    lng = np.ascontiguousarray(lng, dtype=np.complex128)
+    fat, lng = _links_arg(fat), _links_arg(lng)
     _check(_load().hisq_load_links_slab(ctx, t_begin, t_count, _ptr(fat), _ptr(lng), flags), "hisq_load_links_slab")
 
 

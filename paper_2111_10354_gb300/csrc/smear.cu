@@ -21,8 +21,11 @@
 // pipe, which GB300 runs ~60x faster than its FP64 pipe. Inputs and outputs are binary64 either way.
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "trace.h"
+#include "tune.h"
 
 namespace hisq {
 
@@ -30,7 +33,10 @@ bool is_device_ptr(const void* p);
 
 namespace {
 
-constexpr int SMEAR_BLOCK = 128;
+constexpr int SMEAR_BLOCK = 128;      // the conversion and projection kernels
+constexpr int SMEAR_MAX_BLOCK = 256;  // the pass kernels: the tuner picks the block size up to this and one of
+                                      // two register budgets (MINB 1: as many as the code wants; MINB 2:
+                                      // 128 per thread, more resident warps, a few spills)
 
 // One complex entry of an intermediate field: double2 for FP64 arithmetic, float4 (re.hi, re.lo,
 // im.hi, im.lo) for double-float; 16 bytes either way. Fields are stored [entry 0..8][site].
@@ -42,6 +48,12 @@ struct FieldIO<double> {
   __device__ __forceinline__ static cplx<double> ld(const S* p) {
     const S v = __ldg(p);
     return {v.x, v.y};
+  }
+  // the entry, conjugated when c (a sign-bit flip on the integer pipe: the FP64 pipe is the bottleneck)
+  __device__ __forceinline__ static cplx<double> ld_conj_if(const S* p, bool c) {
+    const S v = __ldg(p);
+    const long long m = c ? (long long)0x8000000000000000ull : 0ll;
+    return {v.x, __longlong_as_double(__double_as_longlong(v.y) ^ m)};
   }
   __device__ __forceinline__ static void st(S* p, const cplx<double>& c) { *p = make_double2(c.re, c.im); }
   __device__ __forceinline__ static cplx<double> from_f64(double2 v) { return {v.x, v.y}; }
@@ -55,6 +67,11 @@ struct FieldIO<df64> {
   __device__ __forceinline__ static cplx<df64> ld(const S* p) {
     const S v = __ldg(p);
     return {df64(v.x, v.y), df64(v.z, v.w)};
+  }
+  __device__ __forceinline__ static cplx<df64> ld_conj_if(const S* p, bool c) {
+    const S v = __ldg(p);
+    const unsigned m = c ? 0x80000000u : 0u;
+    return {df64(v.x, v.y), df64(__uint_as_float(__float_as_uint(v.z) ^ m), __uint_as_float(__float_as_uint(v.w) ^ m))};
   }
   __device__ __forceinline__ static void st(S* p, const cplx<df64>& c) {
     *p = make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo);
@@ -77,10 +94,21 @@ __device__ __forceinline__ cplx<T> conj_c(const cplx<T>& a) {
   return {a.re, -a.im};
 }
 
+// m = f[s], or its conjugate transpose when dag
 template <typename T>
-__device__ __forceinline__ void load_m(M3<T>& m, const typename FieldIO<T>::S* f, size_t V, int s) {
+__device__ __forceinline__ void load_m(M3<T>& m, const typename FieldIO<T>::S* f, size_t V, int s, bool dag) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) m.e[k] = FieldIO<T>::ld(f + (size_t)k * V + s);
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      m.e[3 * i + j] = FieldIO<T>::ld_conj_if(f + (size_t)(dag ? 3 * j + i : 3 * i + j) * V + s, dag);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void zero_m(M3<T>& m) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m.e[k] = {FieldIO<T>::zero(), FieldIO<T>::zero()};
 }
 
 template <typename T>
@@ -89,7 +117,7 @@ __device__ __forceinline__ void store_m(typename FieldIO<T>::S* f, size_t V, int
   for (int k = 0; k < 9; ++k) FieldIO<T>::st(f + (size_t)k * V + s, m.e[k]);
 }
 
-// m = a * f0[s] + b * (f1[s] + f2[s]) (f2 may be null: m = a f0 + b f1)
+// m = a * f0[s] + b * (f1[s] + f2[s]); f2 may be null (m = a f0 + b f1), and f1 too (m = a f0)
 template <typename T>
 __device__ __forceinline__ void load_comb(M3<T>& m, const typename FieldIO<T>::S* f0, T a,
                                           const typename FieldIO<T>::S* f1, const typename FieldIO<T>::S* f2, T b,
@@ -98,17 +126,19 @@ __device__ __forceinline__ void load_comb(M3<T>& m, const typename FieldIO<T>::S
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const cplx<T> u = FieldIO<T>::ld(f0 + (size_t)k * V + s);
-    cplx<T> w = FieldIO<T>::ld(f1 + (size_t)k * V + s);
-    if (f2) {
-      const cplx<T> w2 = FieldIO<T>::ld(f2 + (size_t)k * V + s);
-      w.re = w.re + w2.re;
-      w.im = w.im + w2.im;
-    }
     cplx<T> r;
     r.re = fma(a, u.re, z);
     r.im = fma(a, u.im, z);
-    r.re = fma(b, w.re, r.re);
-    r.im = fma(b, w.im, r.im);
+    if (f1) {
+      cplx<T> w = FieldIO<T>::ld(f1 + (size_t)k * V + s);
+      if (f2) {
+        const cplx<T> w2 = FieldIO<T>::ld(f2 + (size_t)k * V + s);
+        w.re = w.re + w2.re;
+        w.im = w.im + w2.im;
+      }
+      r.re = fma(b, w.re, r.re);
+      r.im = fma(b, w.im, r.im);
+    }
     m.e[k] = r;
   }
 }
@@ -124,36 +154,6 @@ __device__ __forceinline__ void mul_nn(M3<T>& c, const M3<T>& a, const M3<T>& b)
       cplx<T> acc{z, z};
 #pragma unroll
       for (int k = 0; k < 3; ++k) cmac(acc, a.e[3 * i + k], b.e[3 * k + j]);
-      c.e[3 * i + j] = acc;
-    }
-}
-
-// c = a^dag b
-template <typename T>
-__device__ __forceinline__ void mul_dn(M3<T>& c, const M3<T>& a, const M3<T>& b) {
-  const T z = FieldIO<T>::zero();
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      cplx<T> acc{z, z};
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cmac(acc, conj_c(a.e[3 * k + i]), b.e[3 * k + j]);
-      c.e[3 * i + j] = acc;
-    }
-}
-
-// c = a b^dag
-template <typename T>
-__device__ __forceinline__ void mul_nd(M3<T>& c, const M3<T>& a, const M3<T>& b) {
-  const T z = FieldIO<T>::zero();
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      cplx<T> acc{z, z};
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cmac(acc, a.e[3 * i + k], conj_c(b.e[3 * j + k]));
       c.e[3 * i + j] = acc;
     }
 }
@@ -222,9 +222,16 @@ __global__ void __launch_bounds__(SMEAR_BLOCK) k_to_fields(const double2* __rest
   FieldIO<T>::st(out + (size_t)e * V + s, FieldIO<T>::from_f64(__ldg(in + (size_t)s * 36 + e)));
 }
 
-// Pass 1: the six one-signed staples of U_mu at every site.
-template <typename T>
-__global__ void __launch_bounds__(SMEAR_BLOCK) k_smear_staples(const typename FieldIO<T>::S* __restrict__ U,
+// Each pass accumulates products A X C of three matrices: A and C are links U_b at the two ends of a
+// staple (conjugate-transposed at load time for the backward half), X is the middle field. One loop
+// iteration handles one (direction, sign), so each kernel holds a single copy of the two 3x3
+// products: the double-float products are long instruction sequences, and one copy keeps the loop
+// inside the instruction cache.
+
+// Pass 1: the six one-signed staples of U_mu at every site, S_{nu,+} at field 2j, S_{nu,-} at 2j+1
+// (nu = transverse(mu, j)).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_staples(const typename FieldIO<T>::S* __restrict__ U,
                                                                typename FieldIO<T>::S* __restrict__ St, Geom g,
                                                                int mu) {
   using S = typename FieldIO<T>::S;
@@ -234,76 +241,75 @@ __global__ void __launch_bounds__(SMEAR_BLOCK) k_smear_staples(const typename Fi
   int c[4];
   lex_coords(g, s, c);
   const S* Umu = U + (size_t)mu * 9 * V;
-  const int s_mu = step(g, s, c[mu], mu, 1);
 #pragma unroll 1
-  for (int j = 0; j < 3; ++j) {
-    const int nu = transverse(mu, j);
+  for (int it = 0; it < 6; ++it) {
+    const int nu = transverse(mu, it >> 1);
+    const bool bwd = it & 1;
     const S* Unu = U + (size_t)nu * 9 * V;
+    // forward: U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag; backward: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+    const int y0 = bwd ? step(g, s, c[nu], nu, -1) : s;
     M3<T> a, b, p, r;
-    // U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
-    load_m(a, Unu, V, s);
-    load_m(b, Umu, V, step(g, s, c[nu], nu, 1));
+    load_m(a, Unu, V, y0, bwd);
+    load_m(b, Umu, V, bwd ? y0 : step(g, s, c[nu], nu, 1), false);
     mul_nn(p, a, b);
-    load_m(a, Unu, V, s_mu);
-    mul_nd(r, p, a);
-    store_m(St + (size_t)(2 * j) * 9 * V, V, s, r);
-    // U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
-    const int m = step(g, s, c[nu], nu, -1);
-    load_m(a, Unu, V, m);
-    load_m(b, Umu, V, m);
-    mul_dn(p, a, b);
-    load_m(a, Unu, V, step(g, m, c[mu], mu, 1));
-    mul_nn(r, p, a);
-    store_m(St + (size_t)(2 * j + 1) * 9 * V, V, s, r);
+    load_m(a, Unu, V, step(g, y0, c[mu], mu, 1), !bwd);
+    zero_m(r);
+    mul_nn_acc(r, p, a);
+    store_m(St + (size_t)it * 9 * V, V, s, r);
   }
 }
 
-// Pass 2: Y_a for the transverse direction a = transverse(mu, blockIdx.y).
-template <typename T>
-__global__ void __launch_bounds__(SMEAR_BLOCK) k_smear_middle(const typename FieldIO<T>::S* __restrict__ U,
+// Pass 2: Y_a for the transverse direction a = transverse(mu, blockIdx.x % 3). The three values of a
+// are neighbouring blocks, so the links and staples of a group of sites are read while in L2.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_middle(const typename FieldIO<T>::S* __restrict__ U,
                                                               const typename FieldIO<T>::S* __restrict__ St,
                                                               typename FieldIO<T>::S* __restrict__ Y, Geom g, int mu,
                                                               double c3, double c5, double c7) {
   using S = typename FieldIO<T>::S;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ai = blockIdx.x % 3;
+  const int s = (blockIdx.x / 3) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   const size_t V = g.V;
-  const int ai = blockIdx.y;
   int c[4];
   lex_coords(g, s, c);
   const S* Umu = U + (size_t)mu * 9 * V;
   const T t5 = FieldIO<T>::coef(c5), t7 = FieldIO<T>::coef(c7);
   M3<T> y;
-  load_m(y, Umu, V, s);
+  load_m(y, Umu, V, s, false);
   scale_m(y, FieldIO<T>::coef(c3));
 #pragma unroll 1
-  for (int bi = 0; bi < 3; ++bi) {
-    if (bi == ai) continue;
-    const int b = transverse(mu, bi), ci = 3 - ai - bi;
+  for (int it = 0; it < 4; ++it) {
+    const int bsel = it >> 1, bi = bsel + (bsel >= ai), ci = 3 - ai - bi;
+    const bool bwd = it & 1;
+    const int b = transverse(mu, bi);
     const S* Ub = U + (size_t)b * 9 * V;
-    const S* Sp = St + (size_t)(2 * ci) * 9 * V;
-    const S* Sm = St + (size_t)(2 * ci + 1) * 9 * V;
+    // forward: U_b(x) X(x+b) U_b(x+mu)^dag; backward: U_b(x-b)^dag X(x-b) U_b(x-b+mu);
+    // X = c5 U_mu + c7 (S_{c,+} + S_{c,-})
+    const int y0 = bwd ? step(g, s, c[b], b, -1) : s;
     M3<T> x, u, p;
-    // U_b(x) X(x+b) U_b(x+mu)^dag, X = c5 U_mu + c7 (S_{c,+} + S_{c,-})
-    load_comb(x, Umu, t5, Sp, Sm, t7, V, step(g, s, c[b], b, 1));
-    load_m(u, Ub, V, s);
+    load_comb(x, Umu, t5, St + (size_t)(2 * ci) * 9 * V, St + (size_t)(2 * ci + 1) * 9 * V, t7, V,
+              bwd ? y0 : step(g, s, c[b], b, 1));
+    load_m(u, Ub, V, y0, bwd);
     mul_nn(p, u, x);
-    load_m(u, Ub, V, step(g, s, c[mu], mu, 1));
-    mul_nd_acc(y, p, u);
-    // U_b(x-b)^dag X(x-b) U_b(x-b+mu)
-    const int m = step(g, s, c[b], b, -1);
-    load_comb(x, Umu, t5, Sp, Sm, t7, V, m);
-    load_m(u, Ub, V, m);
-    mul_dn(p, u, x);
-    load_m(u, Ub, V, step(g, m, c[mu], mu, 1));
+    load_m(u, Ub, V, step(g, y0, c[mu], mu, 1), !bwd);
     mul_nn_acc(y, p, u);
   }
   store_m(Y + (size_t)ai * 9 * V, V, s, y);
 }
 
-// Pass 3: the fat link F_mu and (lng != null) the Naik link L_mu, written in the boundary layout.
 template <typename T>
-__global__ void __launch_bounds__(SMEAR_BLOCK) k_smear_fat(const typename FieldIO<T>::S* __restrict__ U,
+__device__ __forceinline__ void store_link(double2* out, int s, int mu, const M3<T>& m) {
+  double2* o = out + ((size_t)s * 4 + mu) * 9;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) o[k] = FieldIO<T>::to_f64(m.e[k]);
+}
+
+// Pass 3: the fat link F_mu and (lng != null) the Naik link L_mu, written in the boundary layout. The
+// Naik product is a seventh loop iteration, U_mu(x) [cN U_mu(x+mu)] U_mu(x+2mu), into a fresh
+// accumulator.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_fat(const typename FieldIO<T>::S* __restrict__ U,
                                                            const typename FieldIO<T>::S* __restrict__ St,
                                                            const typename FieldIO<T>::S* __restrict__ Y,
                                                            double2* __restrict__ fat, double2* __restrict__ lng,
@@ -315,53 +321,43 @@ __global__ void __launch_bounds__(SMEAR_BLOCK) k_smear_fat(const typename FieldI
   int c[4];
   lex_coords(g, s, c);
   const S* Umu = U + (size_t)mu * 9 * V;
-  const T one = FieldIO<T>::coef(1.0), tL = FieldIO<T>::coef(cL);
+  const T one = FieldIO<T>::coef(1.0), tL = FieldIO<T>::coef(cL), tN = FieldIO<T>::coef(cN);
   const int s_mu = step(g, s, c[mu], mu, 1);
   M3<T> f;
-  load_m(f, Umu, V, s);
+  load_m(f, Umu, V, s, false);
   scale_m(f, FieldIO<T>::coef(c1));
+  const int nit = lng ? 7 : 6;
 #pragma unroll 1
-  for (int ai = 0; ai < 3; ++ai) {
-    const int a = transverse(mu, ai);
-    const S* Ua = U + (size_t)a * 9 * V;
-    const S* Ya = Y + (size_t)ai * 9 * V;
+  for (int it = 0; it < nit; ++it) {
     M3<T> z, u, p;
-    // U_a(x) Z(x+a) U_a(x+mu)^dag, Z = Y_a + cL S_{a,+}
-    const int sp = step(g, s, c[a], a, 1);
-    if (cL != 0.0)
-      load_comb(z, Ya, one, St + (size_t)(2 * ai) * 9 * V, (const S*)nullptr, tL, V, sp);
-    else
-      load_m(z, Ya, V, sp);
-    load_m(u, Ua, V, s);
+    const S* Ua;
+    int y0, sc;
+    bool bwd;
+    if (it < 6) {
+      // forward: U_a(x) Z(x+a) U_a(x+mu)^dag; backward: U_a(x-a)^dag Z(x-a) U_a(x-a+mu);
+      // Z = Y_a + cL S_{a,sign}
+      const int ai = it >> 1, a = transverse(mu, ai);
+      bwd = it & 1;
+      Ua = U + (size_t)a * 9 * V;
+      y0 = bwd ? step(g, s, c[a], a, -1) : s;
+      sc = step(g, y0, c[mu], mu, 1);
+      load_comb(z, Y + (size_t)ai * 9 * V, one, cL != 0.0 ? St + (size_t)it * 9 * V : (const S*)nullptr,
+                (const S*)nullptr, tL, V, bwd ? y0 : step(g, s, c[a], a, 1));
+    } else {
+      store_link(fat, s, mu, f);
+      zero_m(f);
+      bwd = false;
+      Ua = Umu;
+      y0 = s;
+      sc = step(g, s_mu, c[mu] + 1 < g.L[mu] ? c[mu] + 1 : 0, mu, 1);
+      load_comb(z, Umu, tN, (const S*)nullptr, (const S*)nullptr, tN, V, s_mu);
+    }
+    load_m(u, Ua, V, y0, bwd);
     mul_nn(p, u, z);
-    load_m(u, Ua, V, s_mu);
-    mul_nd_acc(f, p, u);
-    // U_a(x-a)^dag Z(x-a) U_a(x-a+mu), Z = Y_a + cL S_{a,-}
-    const int m = step(g, s, c[a], a, -1);
-    if (cL != 0.0)
-      load_comb(z, Ya, one, St + (size_t)(2 * ai + 1) * 9 * V, (const S*)nullptr, tL, V, m);
-    else
-      load_m(z, Ya, V, m);
-    load_m(u, Ua, V, m);
-    mul_dn(p, u, z);
-    load_m(u, Ua, V, step(g, m, c[mu], mu, 1));
+    load_m(u, Ua, V, sc, !bwd && it < 6);
     mul_nn_acc(f, p, u);
   }
-  double2* out = fat + ((size_t)s * 4 + mu) * 9;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) out[k] = FieldIO<T>::to_f64(f.e[k]);
-  if (lng) {
-    M3<T> a, b, p;
-    load_m(a, Umu, V, s);
-    load_m(b, Umu, V, s_mu);
-    mul_nn(p, a, b);
-    load_m(a, Umu, V, step(g, s_mu, (c[mu] + 1) % g.L[mu], mu, 1));
-    mul_nn(f, p, a);
-    scale_m(f, FieldIO<T>::coef(cN));
-    double2* lo = lng + ((size_t)s * 4 + mu) * 9;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) lo[k] = FieldIO<T>::to_f64(f.e[k]);
-  }
+  store_link(lng ? lng : fat, s, mu, f);
 }
 
 // W -> W (W^dag W)^{-1/2} for every link, in FP64. The inverse square root of the Hermitian
@@ -442,26 +438,59 @@ __global__ void __launch_bounds__(SMEAR_BLOCK) k_project_u3(double2* out, const 
     }
 }
 
+// One pass kernel with its launch shape chosen by the tuner: a register budget (MINB 1 or 2) and the
+// block size. All three passes are idempotent (their outputs are not read), so they can be timed.
+template <typename Kern, typename Launch>
+int launch_pass(hisq_ctx* ctx, const char* key, Kern k1, Kern k2, Launch launch) {
+  TuneVariant v[2] = {{(const void*)k1, [&](int b) { return launch(k1, b); }},
+                      {(const void*)k2, [&](int b) { return launch(k2, b); }}};
+  int vi = 0, block = SMEAR_BLOCK;
+  int rc = tuned_variant(ctx, key, v, 2, &vi, &block);
+  if (rc) return rc;
+  HISQ_CUDA(v[vi].run(block));
+  note_launch(ctx);
+  return HISQ_OK;
+}
+
+inline unsigned blocks_for(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
 template <typename T>
 int smear_level(hisq_ctx* ctx, double* fat, double* lng, const double* thin, const hisq_smear_coeffs& cf) {
   using S = typename FieldIO<T>::S;
-  const Geom& g = ctx->g;
+  const Geom g = ctx->g;
   const size_t V = g.V;
+  cudaStream_t st = ctx->stream;
   S* U = (S*)workspace(ctx, "smear_thin", 36 * V * sizeof(S));
-  S* St = (S*)workspace(ctx, "smear_staples", 54 * V * sizeof(S));
+  S* Sf = (S*)workspace(ctx, "smear_staples", 54 * V * sizeof(S));
   S* Y = (S*)workspace(ctx, "smear_middle", 27 * V * sizeof(S));
-  if (!U || !St || !Y) return set_error(HISQ_ENOMEM, "smearing workspaces (%zu bytes)", 117 * V * sizeof(S));
-  const unsigned nb = (unsigned)((V + SMEAR_BLOCK - 1) / SMEAR_BLOCK);
-  k_to_fields<T><<<dim3(nb, 36), SMEAR_BLOCK, 0, ctx->stream>>>((const double2*)thin, U, g.V);
-  for (int mu = 0; mu < 4; ++mu) {
-    k_smear_staples<T><<<nb, SMEAR_BLOCK, 0, ctx->stream>>>(U, St, g, mu);
-    k_smear_middle<T><<<dim3(nb, 3), SMEAR_BLOCK, 0, ctx->stream>>>(U, St, Y, g, mu, cf.three_staple,
-                                                                    cf.five_staple, cf.seven_staple);
-    k_smear_fat<T><<<nb, SMEAR_BLOCK, 0, ctx->stream>>>(U, St, Y, (double2*)fat, (double2*)lng, g, mu,
-                                                        cf.one_link, cf.lepage, cf.naik);
-  }
-  note_launch(ctx, 13);
+  if (!U || !Sf || !Y) return set_error(HISQ_ENOMEM, "smearing workspaces (%zu bytes)", 117 * V * sizeof(S));
+  k_to_fields<T><<<dim3(blocks_for(V, SMEAR_BLOCK), 36), SMEAR_BLOCK, 0, st>>>((const double2*)thin, U, g.V);
   HISQ_CUDA(cudaGetLastError());
+  note_launch(ctx);
+  const bool dd = std::is_same<T, df64>::value;
+  const double c3 = cf.three_staple, c5 = cf.five_staple, c7 = cf.seven_staple, c1 = cf.one_link, cL = cf.lepage,
+               cN = cf.naik;
+  double2 *f2 = (double2*)fat, *l2 = (double2*)lng;
+  for (int mu = 0; mu < 4; ++mu) {
+    int rc = launch_pass(ctx, dd ? "smear/staples/df64" : "smear/staples/f64", k_smear_staples<T, 1>,
+                         k_smear_staples<T, 2>, [&](decltype(&k_smear_staples<T, 1>) k, int b) {
+                           k<<<blocks_for(V, b), b, 0, st>>>(U, Sf, g, mu);
+                           return cudaGetLastError();
+                         });
+    if (rc) return rc;
+    rc = launch_pass(ctx, dd ? "smear/middle/df64" : "smear/middle/f64", k_smear_middle<T, 1>, k_smear_middle<T, 2>,
+                     [&](decltype(&k_smear_middle<T, 1>) k, int b) {
+                       k<<<3 * blocks_for(V, b), b, 0, st>>>(U, Sf, Y, g, mu, c3, c5, c7);
+                       return cudaGetLastError();
+                     });
+    if (rc) return rc;
+    rc = launch_pass(ctx, dd ? "smear/fat/df64" : "smear/fat/f64", k_smear_fat<T, 1>, k_smear_fat<T, 2>,
+                     [&](decltype(&k_smear_fat<T, 1>) k, int b) {
+                       k<<<blocks_for(V, b), b, 0, st>>>(U, Sf, Y, f2, l2, g, mu, c1, cL, cN);
+                       return cudaGetLastError();
+                     });
+    if (rc) return rc;
+  }
   return HISQ_OK;
 }
 
