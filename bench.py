@@ -53,7 +53,8 @@ def parse():
                     help="time the steps only: no e2e, comparison solves or CPU baseline (for profiler launch lists)")
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
     ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-df64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8",
-                                                   "cg-f32-nr8", "ptc", "fcg", "batch", "smear-f64", "smear-df64"],
+                                                   "cg-f32-nr8", "ptc", "fcg", "batch", "smear-f64", "smear-df64",
+                                                   "dslash-f16-nr16-tc", "dslash-f16-nr16-cc"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned", "smear"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
@@ -507,8 +508,24 @@ def row_multirhs(h, torch, hin):
     L = (48, 48, 48, 12)
     fat, lng = hin.gen_links(L, 1002, 0.3, 0.1)
     stream = torch.cuda.Stream()
-    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16, h.HISQ_DF64), stream=stream).load(fat, lng)
+    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16, h.HISQ_BF16, h.HISQ_DF64), stream=stream).load(fat, lng)
     peak, _ = peaks()
+    dims = "x".join(map(str, L))
+    # 16-bit storage, 8 or more vectors: the tensor-core and the CUDA-core forms, each forced
+    for prec, name in ((h.HISQ_F16, "f16"), (h.HISQ_BF16, "bf16")):
+        for n in (8, 16, 32, 64):
+            by = lat.dslash_bytes(prec, n)
+            best = {}
+            for path, form in ((1, "cuda-core"), (2, "tensor-core")):
+                h.hisq_tune_load(lat.ctx, "dslash_path/l%d/n%d %s -> %d\n" % (prec, n, dims, path))
+                ms = time_dslash(torch, lat, prec, n, 10, stream)
+                best[path] = ms
+                print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": name, "nrhs": n, "form": form,
+                                  "dslash_us": round(ms * 1e3, 1), "dslash_GBps": round(by / ms / 1e6, 1),
+                                  "dslash_frac_hbm": round(by / ms / 1e6 / peak, 3),
+                                  "dslash_GFLOPs": round(1146 * n * lat.half / (ms * 1e-3) / 1e9, 1)}), flush=True)
+            # keep the faster form, as the tuner would
+            h.hisq_tune_load(lat.ctx, "dslash_path/l%d/n%d %s -> %d\n" % (prec, n, dims, min(best, key=best.get)))
     # Dslash only at FP16 storage (FP32 arithmetic) and FP64
     for prec, name, ns in ((h.HISQ_F16, "f16", (1, 2, 4, 8, 16)), (h.HISQ_F64, "f64", (1, 2, 4, 8))):
         for n in ns:
@@ -768,9 +785,12 @@ def run_kernel_case(name):
             lat.compress_long(-1.0 / 24.0)
         lat.load(fat, lng)
         prec = {"dslash-f64": h.HISQ_F64, "dslash-df64": h.HISQ_DF64, "dslash-f16": h.HISQ_F16,
-                "dslash-f32-comp": h.HISQ_F32,
-                "dslash-f32-nr8": h.HISQ_F32}[name]
-        ms = time_dslash(torch, lat, prec, 8 if name.endswith("nr8") else 1, 4, stream)
+                "dslash-f32-comp": h.HISQ_F32, "dslash-f32-nr8": h.HISQ_F32, "dslash-f16-nr16-tc": h.HISQ_F16,
+                "dslash-f16-nr16-cc": h.HISQ_F16}[name]
+        nrhs = 8 if name.endswith("nr8") else (16 if "nr16" in name else 1)
+        if "nr16" in name:  # the tensor-core or the CUDA-core form, forced
+            h.hisq_tune_load(lat.ctx, "dslash_path/l%d/n16 48x48x48x12 -> %d\n" % (prec, 2 if name.endswith("tc") else 1))
+        ms = time_dslash(torch, lat, prec, nrhs, 4, stream)
         print(json.dumps({"case": name, "us": round(ms * 1e3, 2)}))
     elif name == "cg-f32-nr8":
         L = (48, 48, 48, 12)

@@ -16,6 +16,7 @@ int dslash_launch_f32(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_f16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_bf16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_df64(hisq_ctx* ctx, int sp, const DslashCall& c);
+int dslash_mma_launch(hisq_ctx* ctx, int prec, const DslashCall& c);
 
 static thread_local char g_last_error[512] = "";
 
@@ -50,8 +51,7 @@ void* workspace(hisq_ctx* ctx, const char* name, size_t bytes) {
   return b.ptr;
 }
 
-int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
-  if (!ctx->links[lp]) return set_error(HISQ_EINVAL, "link precision %d is not resident", lp);
+static int dslash_launch_core(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
   switch (lp) {
     case HISQ_F64: return dslash_launch_f64(ctx, sp, c);
     case HISQ_F32: return dslash_launch_f32(ctx, sp, c);
@@ -60,6 +60,53 @@ int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
     case HISQ_DF64: return dslash_launch_df64(ctx, sp, c);
   }
   return set_error(HISQ_EINVAL, "bad precision %d", lp);
+}
+
+// 16-bit storage with 8 or more right-hand sides and the plain epilogue also has a tensor-core form
+// (dslash_mma.cu). The first such call times both forms (each after its own launch-shape tuning; the
+// plain Dslash does not read its output, so running it twice is harmless) and keeps the faster one
+// per (precision, rhs count) in the tune cache: 1 = CUDA cores, 2 = tensor cores.
+static int dslash_launch_16bit_multi(hisq_ctx* ctx, int lp, const DslashCall& c) {
+  char key[48];
+  snprintf(key, sizeof key, "dslash_path/l%d/n%d", lp, c.nrhs);
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) {
+    int v = it->second < 0 ? -it->second : it->second;  // negative: loaded from a report, unchecked
+    if (v == 1 || v == 2) {
+      it->second = v;
+      return v == 2 ? dslash_mma_launch(ctx, lp, c) : dslash_launch_core(ctx, lp, lp, c);
+    }
+    ctx->tune.erase(it);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  HISQ_CUDA(cudaStreamIsCapturing(ctx->stream, &cap));
+  if (!ctx->autotune || cap != cudaStreamCaptureStatusNone) return dslash_launch_core(ctx, lp, lp, c);
+  cudaEvent_t e[3];
+  for (auto& ev : e) HISQ_CUDA(cudaEventCreate(&ev));
+  float ms[2] = {0.f, 0.f};
+  int rc = HISQ_OK;
+  for (int path = 0; path < 2 && rc == HISQ_OK; ++path) {
+    auto run = [&]() { return path == 1 ? dslash_mma_launch(ctx, lp, c) : dslash_launch_core(ctx, lp, lp, c); };
+    rc = run();  // tunes this form's launch shape
+    if (rc != HISQ_OK) break;
+    cudaEventRecord(e[0], ctx->stream);
+    rc = run();
+    cudaEventRecord(e[1], ctx->stream);
+    if (rc == HISQ_OK && cudaEventSynchronize(e[1]) == cudaSuccess) cudaEventElapsedTime(&ms[path], e[0], e[1]);
+  }
+  for (auto& ev : e) cudaEventDestroy(ev);
+  if (rc != HISQ_OK) return rc;
+  HISQ_CUDA(cudaGetLastError());
+  ctx->tune[key] = ms[1] < ms[0] ? 2 : 1;
+  return HISQ_OK;  // the output holds the last (tensor-core) form's result, equal to the other's
+}
+
+int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
+  if (!ctx->links[lp]) return set_error(HISQ_EINVAL, "link precision %d is not resident", lp);
+  const bool compressed = ctx->naik != 0.0 && ctx->long12[lp] != nullptr;
+  if ((lp == HISQ_F16 || lp == HISQ_BF16) && sp == lp && c.epi == EPI_PLAIN && c.nrhs >= 8 && !compressed)
+    return dslash_launch_16bit_multi(ctx, lp, c);
+  return dslash_launch_core(ctx, lp, sp, c);
 }
 
 double dslash_bytes(const hisq_ctx* ctx, int lp, int sp, int nrhs) {
