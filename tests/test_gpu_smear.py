@@ -102,7 +102,7 @@ def test_project_u3_singular_link_is_an_error(hisq):
     assert np.array_equal(got[7, 2], W[7, 2])
     ok = np.ones(got.shape[:2], bool)
     ok[7, 2] = False
-    assert rel_err(got[ok], sm.project_u3(W)[ok]) <= 1e-13
+    assert rel_err(got[ok], sm.project_u3(W[ok])) <= 1e-13
 
 
 @pytest.mark.parametrize("L", LATTICES[:3])
@@ -190,3 +190,35 @@ def test_argument_errors(hisq):
         with pytest.raises(hisq.HisqError) as e:
             f()
         assert e.value.code == hisq.HISQ_EINVAL, what
+
+
+@pytest.mark.parametrize("prec", [0, 4])
+def test_every_launch_form_matches_oracle(hisq, prec):
+    """Each pass kernel in both register budgets (form 0: as many registers as the code wants, form 1: 128)
+    and at several block sizes, forced through loaded tune entries, and the untuned fallback with the
+    autotuner off, against the oracle."""
+    import torch
+    L = (6, 4, 4, 6)
+    U = links(L, 91)
+    F, Lg = sm.smear(L, U, **RANDOM)
+    u = dev(U)
+    dims = "%dx%dx%dx%d" % L
+    name = "df64" if prec == 4 else "f64"
+    for vi in (0, 1):
+        for block in (64, 96, 256):
+            lat = hisq.Lattice(L, precs=(0,))
+            rep = "".join("smear/%s/%s %s -> %d\n" % (k, name, dims, vi * 10000 + block)
+                          for k in ("staples", "middle", "fat"))
+            assert hisq.hisq_tune_load(lat.ctx, rep) == 3
+            fat, lng = empty_links(L), empty_links(L)
+            lat.smear(fat, lng, u, RANDOM, prec)
+            torch.cuda.synchronize()
+            assert rel_err(fat.cpu().numpy(), F) <= TOL[prec], (vi, block)
+            assert rel_err(lng.cpu().numpy(), Lg) <= TOL[prec], (vi, block)
+            assert hisq.hisq_tune_report(lat.ctx).count("-> %d" % (vi * 10000 + block)) == 3
+    lat = hisq.Lattice(L, precs=(0,))
+    hisq.hisq_set_autotune(lat.ctx, False)
+    fat, lng = empty_links(L), empty_links(L)
+    lat.smear(fat, lng, u, RANDOM, prec)
+    torch.cuda.synchronize()
+    assert rel_err(fat.cpu().numpy(), F) <= TOL[prec]
