@@ -202,12 +202,10 @@ int launch_mma_t(hisq_ctx* ctx, int prec, const DslashCall& c) {
   a.rhs_stride = c.rhs_stride;
   a.skip = c.skip;
   const int nrhs = c.nrhs;
-  static bool attr_set = false;  // per instantiation: allow the tile's shared memory (above 48 KB)
-  if (!attr_set) {
-    HISQ_CUDA(cudaFuncSetAttribute(dslash_mma_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sizeof(MmaSmem)));
-    attr_set = true;
-  }
+  // the tile's shared memory is above the 48 KB default (a host-side attribute of the function on the
+  // current device, set before every launch: cheap, and right whichever device the context is on)
+  HISQ_CUDA(cudaFuncSetAttribute(dslash_mma_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(MmaSmem)));
   int per_sm = 0;
   HISQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dslash_mma_kernel<H>, MMA_THREADS,
                                                           sizeof(MmaSmem)));
