@@ -69,16 +69,16 @@ __device__ __forceinline__ unsigned bfrag(unsigned w, int part, bool backward) {
   return part ? (sw ^ 0x80000000u) : (w ^ 0x80008000u);        // {-re, -im} or {im, -re}
 }
 
-// A block of 256 threads takes a tile of MT = 16 consecutive output sites at a time and stages, in
+// A block of 16 * MT threads takes a tile of MT consecutive output sites at a time and stages, in
 // shared memory, the neighbour index and the link of every (hop, site) -- thread (hop, site) -- and
 // the vectors of the current group of 16 at every (hop, site) -- thread (vector, site) walks the 16
 // hops -- with asynchronous copies, neighbouring threads on neighbouring sites, so the global reads
-// are coalesced as in the CUDA-core kernel. Each warp then takes two sites of the tile: B fragments
-// from the staged links, A fragments with ldmatrix.x4 (one 16-byte row per vector: its 3 complex
-// colour entries and a zero word), 8 mma per site and group of 16 vectors.
-constexpr int MT = 16;           // output sites per tile
-constexpr int MMA_THREADS = 256;  // = 16 hops (or vectors) x MT sites
-
+// are coalesced as in the CUDA-core kernel. Each warp then takes sites of the tile: it reads the
+// site's link words and its A fragments (ldmatrix.x4; one 16-byte row per vector: its 3 complex
+// colour entries and a zero word) for all 16 hops, then issues the 8 mma of a group of 16 vectors.
+// MT output sites per tile (16 or 8), 16 * MT threads per block: fewer sites per tile use less
+// shared memory and let more blocks share an SM.
+template <int MT>
 struct MmaSmem {
   uint4 av[16][MT][16];       // [hop][site][vector slot]: slot = vector ^ (site & 7)
   unsigned lk[16][MT][12];    // [hop][site]: the 9 link entries, rows padded to 48 bytes
@@ -98,10 +98,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-template <typename H>
-__global__ void __launch_bounds__(MMA_THREADS) dslash_mma_kernel(const DslashKArgs k, int nrhs) {
+template <typename H, int MT>
+__global__ void __launch_bounds__(16 * MT) dslash_mma_kernel(const DslashKArgs k, int nrhs) {
+  constexpr int MMA_THREADS = 16 * MT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  MmaSmem& sm = *reinterpret_cast<MmaSmem*>(smem_raw);
+  MmaSmem<MT>& sm = *reinterpret_cast<MmaSmem<MT>*>(smem_raw);
   if (k.skip && *k.skip) return;
   const Geom& g = k.g;
   const int p = k.out_parity;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(MMA_THREADS) dslash_mma_kernel(const DslashKAr
   const size_t stride = k.rhs_stride;
   const int ntiles = (g.half + MT - 1) / MT;
   // staging roles: site ts of the tile; hop th (neighbour, link) or vector tr (vectors)
-  const int ts = tid & (MT - 1), th = tid >> 4, tr = tid >> 4;
+  const int ts = tid % MT, th = tid / MT, tr = tid / MT;
   const int hmu = (th >> 1) & 3, hkind = th >> 3, hbwd = th & 1;
   const int hstep = (hkind ? 3 : 1) * (hbwd ? -1 : 1);
   const char* hblk = k.links + (size_t)(((hbwd ? 1 - p : p) * 2 + hkind) * 4 + hmu) * k.blk_bytes;
@@ -169,17 +170,20 @@ __global__ void __launch_bounds__(MMA_THREADS) dslash_mma_kernel(const DslashKAr
       for (int s = warp; s < MT; s += MMA_THREADS / 32) {
         const int cb = cb0 + s;
         if (cb >= g.half) break;  // warp-uniform
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        // all shared-memory reads of the site first (the asm statements keep their order, so the
+        // eight ldmatrix are issued back to back and their latencies overlap), then the 8 products
+        unsigned a[8][4], b[8][2];
 #pragma unroll
         for (int pr = 0; pr < 8; ++pr) {
-          const unsigned b0 = bval ? bfrag(sm.lk[2 * pr][s][3 * j + q], part, false) : 0u;
-          const unsigned b1 = bval ? bfrag(sm.lk[2 * pr + 1][s][3 * q + j], part, true) : 0u;
-          unsigned a0, a1, a2, a3;
+          b[pr][0] = bval ? bfrag(sm.lk[2 * pr][s][3 * j + q], part, false) : 0u;
+          b[pr][1] = bval ? bfrag(sm.lk[2 * pr + 1][s][3 * q + j], part, true) : 0u;
           asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                       : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
+                       : "=r"(a[pr][0]), "=r"(a[pr][1]), "=r"(a[pr][2]), "=r"(a[pr][3])
                        : "r"(smem_u32(&sm.av[2 * pr + lhop][s][lrow ^ (s & 7)])));
-          Mma<H>::run(d, a0, a1, a2, a3, b0, b1);
         }
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int pr = 0; pr < 8; ++pr) Mma<H>::run(d, a[pr][0], a[pr][1], a[pr][2], a[pr][3], b[pr][0], b[pr][1]);
         if (q < 3) {
           if (r0 + gq < nrhs) out[((size_t)(r0 + gq) * stride + cb) * 3 + q] = Mma<H>::pack(d[0], d[1]);
           if (r0 + gq + 8 < nrhs) out[((size_t)(r0 + gq + 8) * stride + cb) * 3 + q] = Mma<H>::pack(d[2], d[3]);
@@ -188,6 +192,28 @@ __global__ void __launch_bounds__(MMA_THREADS) dslash_mma_kernel(const DslashKAr
       __syncthreads();  // the tile's vectors (and, after the last group, its links) are reused next
     }
   }
+}
+
+// One tile size as a tuner candidate. The block size is fixed by the tile (16 threads per site), so
+// the tuner's block-size argument is ignored and the choice is between the two tile sizes.
+template <typename H, int MT>
+TuneVariant mma_variant(hisq_ctx* ctx, const DslashKArgs& a, int nrhs) {
+  return TuneVariant{(const void*)dslash_mma_kernel<H, MT>, [ctx, &a, nrhs](int) -> cudaError_t {
+                       // shared memory above the 48 KB default: a host-side attribute of the function on the
+                       // current device, set before every launch (cheap, right on whichever device)
+                       cudaError_t e = cudaFuncSetAttribute(dslash_mma_kernel<H, MT>,
+                                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                            (int)sizeof(MmaSmem<MT>));
+                       if (e != cudaSuccess) return e;
+                       int per_sm = 0;
+                       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dslash_mma_kernel<H, MT>, 16 * MT,
+                                                                     sizeof(MmaSmem<MT>));
+                       const int tiles = (ctx->g.half + MT - 1) / MT;
+                       int grid = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+                       if (grid > tiles) grid = tiles;
+                       dslash_mma_kernel<H, MT><<<grid, 16 * MT, sizeof(MmaSmem<MT>), ctx->stream>>>(a, nrhs);
+                       return cudaGetLastError();
+                     }};
 }
 
 template <typename H>
@@ -202,18 +228,13 @@ int launch_mma_t(hisq_ctx* ctx, int prec, const DslashCall& c) {
   a.rhs_stride = c.rhs_stride;
   a.skip = c.skip;
   const int nrhs = c.nrhs;
-  // the tile's shared memory is above the 48 KB default (a host-side attribute of the function on the
-  // current device, set before every launch: cheap, and right whichever device the context is on)
-  HISQ_CUDA(cudaFuncSetAttribute(dslash_mma_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(MmaSmem)));
-  int per_sm = 0;
-  HISQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dslash_mma_kernel<H>, MMA_THREADS,
-                                                          sizeof(MmaSmem)));
-  const int tiles = (ctx->g.half + MT - 1) / MT;
-  int grid = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
-  if (grid > tiles) grid = tiles;
-  dslash_mma_kernel<H><<<grid, MMA_THREADS, sizeof(MmaSmem), ctx->stream>>>(a, nrhs);
-  HISQ_CUDA(cudaGetLastError());
+  char key[48];
+  snprintf(key, sizeof key, "dslash_mma/l%d/n%d", prec, nrhs);
+  TuneVariant v[2] = {mma_variant<H, 16>(ctx, a, nrhs), mma_variant<H, 8>(ctx, a, nrhs)};
+  int vi = 0, block = 0;
+  int rc = tuned_variant(ctx, key, v, 2, &vi, &block);
+  if (rc != HISQ_OK) return rc;
+  HISQ_CUDA(v[vi].run(block));
   note_launch(ctx);
   return HISQ_OK;
 }
