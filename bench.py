@@ -189,6 +189,24 @@ def oracle_sample(fat, lng, b, target_s: float = 12.0):
     return bytes_ / dt / 1e9, dt, iters, threads
 
 
+def oracle_solve(fat, lng, b, tol: float = 1e-12, maxiter: int = 600):
+    """The oracle's FP64 CG on the same lattice and source, run to convergence (relative residual tol):
+    the timed CPU baseline, and the solution every GPU solve's final error is stated against.
+    Returns (GB/s of Dslash algorithmic bytes at FP64, seconds, iterations, threads, x)."""
+    import oracle
+    oracle.build()
+    threads = omp_threads()
+    L = DIMS
+    ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
+    half = int(np.prod(L)) // 2
+    t0 = time.perf_counter()
+    x, its = oracle.cg(L, ff, lf, MASS, b[0], tol=tol, maxiter=maxiter)
+    dt = time.perf_counter() - t0
+    iters = its if its >= 0 else maxiter
+    bytes_ = 2 * (iters + 1) * half * (16 * 18 + 12) * 8.0
+    return bytes_ / dt / 1e9, dt, iters, threads, (x if its >= 0 else None)
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU FP64 oracle, as it stands, on the host cores (rank 0 only)."""
     if rank != 0:
@@ -375,6 +393,7 @@ def run_ours(args, rank, world, local):
     # double-float operator (plain CG, and FP32 inner with double-float reliable updates); every solve is
     # judged by its true residual
     cmp = {}
+    sols = {}  # GPU solutions at the benchmark's mass, for their error against the oracle's solution
     for m in (0.01, 0.002):
         row = {}
         for name, o in (("mixed_f32", dict(inner_prec=h.HISQ_F32)), ("mixed_f16", dict(inner_prec=h.HISQ_F16)),
@@ -389,6 +408,8 @@ def run_ours(args, rank, world, local):
             rc, st = lat.cg(xs, b, m, TOL, 20000, **o)
             dt = time.perf_counter() - t0
             row[name] = {"s": round(dt, 4), "iters": st["iters"], "true_res": st["true_rel_residual"]}
+            if m == MASS:
+                sols[name] = xs.cpu().numpy()[0]
         cmp["m=%g" % m] = row
     # the same solves with compressed long links (two rows stored, third rebuilt in the kernel)
     lat.compress_long(-1.0 / 24.0).load(fat, lng)
@@ -404,6 +425,8 @@ def run_ours(args, rank, world, local):
             rc, st = lat.cg(xs, b, m, TOL, 20000, **o)
             dt = time.perf_counter() - t0
             cmp["m=%g" % m][name] = {"s": round(dt, 4), "iters": st["iters"], "true_res": st["true_rel_residual"]}
+            if m == MASS:
+                sols[name] = xs.cpu().numpy()[0]
     ms_comp = time_dslash(torch, lat, h.HISQ_F32, 1, reps, stream)
 
     if rank != 0:
@@ -412,10 +435,16 @@ def run_ours(args, rank, world, local):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        gbs, dt, it, threads = oracle_sample(fat, lng, b_np, 12.0)
+        # the oracle's FP64 CG on the same source, to a 1e-12 relative residual: the timed baseline, and
+        # the solution each GPU solve at this mass is compared with (final error per solve)
+        gbs, dt, it, threads, x_or = oracle_solve(fat, lng, b_np)
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
-               "sample": "oracle FP64 CG on 48x48x48x12 m=0.01: %d iterations (%d Dslash) in %.1f s" % (
-                   it, 2 * (it + 1), dt)}
+               "sample": "oracle FP64 CG on 48x48x48x12 m=%g to a 1e-12 relative residual: %d iterations "
+                         "(%d Dslash) in %.1f s" % (MASS, it, 2 * (it + 1), dt)}
+        if x_or is not None:
+            nx = np.linalg.norm(x_or)
+            for name, xg in sols.items():
+                cmp["m=%g" % MASS][name]["final_err_vs_oracle"] = float("%.3g" % (np.linalg.norm(xg - x_or) / nx))
         # the same oracle on one host core
         all_threads = omp_threads()
         omp_threads(1)
