@@ -360,35 +360,36 @@ __global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_fat(const typen
   store_link(lng ? lng : fat, s, mu, f);
 }
 
-// W -> W (W^dag W)^{-1/2} for every link, in FP64. The inverse square root of the Hermitian
+// W -> W (W^dag W)^{-1/2} for every link (matrix products in T, eigenvalues in FP64). The inverse square root of the Hermitian
 // Q = W^dag W is the polynomial f0 + f1 Q + f2 Q^2 that takes the value g^{-1/2} at each eigenvalue g
 // of Q (Cayley-Hamilton); with s_i = sqrt(g_i), u = s1 + s2 + s3, v = s1 s2 + s1 s3 + s2 s3, w = s1 s2 s3:
 //   f0 = (u v^2 - w (u^2 + v)) / d,  f1 = (2 u v - u^3 - w) / d,  f2 = u / d,  d = w (u v - w).
 // The eigenvalues come from the trigonometric solution of the characteristic cubic of Q - (tr Q / 3).
 // A link whose Q is not positive definite (or not finite) sets bit 4 of *flag and is copied unchanged.
+template <typename T>
 __global__ void __launch_bounds__(SMEAR_BLOCK) k_project_u3(double2* out, const double2* in, long long nlinks,
                                                             int* flag) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nlinks) return;
-  cplx<double> W[9];
+  const T z = FieldIO<T>::zero();
+  cplx<T> W[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const double2 v = in[i * 9 + k];
-    W[k] = {v.x, v.y};
-  }
-  cplx<double> Q[9];
+  for (int k = 0; k < 9; ++k) W[k] = FieldIO<T>::from_f64(in[i * 9 + k]);
+  cplx<T> Q[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      cplx<double> acc{0.0, 0.0};
+      cplx<T> acc{z, z};
 #pragma unroll
       for (int k = 0; k < 3; ++k) cmac(acc, conj_c(W[3 * k + a]), W[3 * k + b]);
       Q[3 * a + b] = acc;
     }
-  const double c0 = (Q[0].re + Q[4].re + Q[8].re) / 3.0;
-  const double d0 = Q[0].re - c0, d1 = Q[4].re - c0, d2 = Q[8].re - c0;
-  const cplx<double> q01 = Q[1], q02 = Q[2], q12 = Q[5];
+  // the eigenvalues (a few scalars) in FP64 whatever the arithmetic of the matrix products
+  const double c0 = ((double)Q[0].re + (double)Q[4].re + (double)Q[8].re) / 3.0;
+  const double d0 = (double)Q[0].re - c0, d1 = (double)Q[4].re - c0, d2 = (double)Q[8].re - c0;
+  const cplx<double> q01{(double)Q[1].re, (double)Q[1].im}, q02{(double)Q[2].re, (double)Q[2].im},
+      q12{(double)Q[5].re, (double)Q[5].im};
   const double n01 = q01.re * q01.re + q01.im * q01.im, n02 = q02.re * q02.re + q02.im * q02.im,
                n12 = q12.re * q12.re + q12.im * q12.im;
   const double p = (d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * (n01 + n02 + n12)) / 6.0;
@@ -409,32 +410,33 @@ __global__ void __launch_bounds__(SMEAR_BLOCK) k_project_u3(double2* out, const 
   if (!(g[0] > 0.0 && g[1] > 0.0 && g[2] > 0.0 && isfinite(g[0] + g[1] + g[2]))) {
     atomicOr(flag, 4);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) out[i * 9 + k] = make_double2(W[k].re, W[k].im);
+    for (int k = 0; k < 9; ++k) out[i * 9 + k] = in[i * 9 + k];
     return;
   }
   const double s0 = sqrt(g[0]), s1 = sqrt(g[1]), s2 = sqrt(g[2]);
   const double u = s0 + s1 + s2, v = s0 * s1 + s0 * s2 + s1 * s2, w = s0 * s1 * s2;
   const double inv_d = 1.0 / (w * (u * v - w));
-  const double f0 = (u * v * v - w * (u * u + v)) * inv_d, f1 = (2.0 * u * v - u * u * u - w) * inv_d, f2 = u * inv_d;
+  const T f0 = FieldIO<T>::coef((u * v * v - w * (u * u + v)) * inv_d),
+          f1 = FieldIO<T>::coef((2.0 * u * v - u * u * u - w) * inv_d), f2 = FieldIO<T>::coef(u * inv_d);
   // X = f0 + f1 Q + f2 Q^2
-  cplx<double> X[9];
+  cplx<T> X[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      cplx<double> q2{0.0, 0.0};
+      cplx<T> q2{z, z};
 #pragma unroll
       for (int k = 0; k < 3; ++k) cmac(q2, Q[3 * a + k], Q[3 * k + b]);
-      X[3 * a + b] = {f1 * Q[3 * a + b].re + f2 * q2.re + (a == b ? f0 : 0.0), f1 * Q[3 * a + b].im + f2 * q2.im};
+      X[3 * a + b] = {fma(f1, Q[3 * a + b].re, fma(f2, q2.re, a == b ? f0 : z)), fma(f1, Q[3 * a + b].im, fma(f2, q2.im, z))};
     }
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      cplx<double> acc{0.0, 0.0};
+      cplx<T> acc{z, z};
 #pragma unroll
       for (int k = 0; k < 3; ++k) cmac(acc, W[3 * a + k], X[3 * k + b]);
-      out[i * 9 + 3 * a + b] = make_double2(acc.re, acc.im);
+      out[i * 9 + 3 * a + b] = FieldIO<T>::to_f64(acc);
     }
 }
 
@@ -494,10 +496,14 @@ int smear_level(hisq_ctx* ctx, double* fat, double* lng, const double* thin, con
   return HISQ_OK;
 }
 
-int launch_project(hisq_ctx* ctx, double* out, const double* in) {
+// The projection with its matrix products in FP64 or (prec HISQ_DF64) double-float.
+int launch_project(hisq_ctx* ctx, double* out, const double* in, int prec) {
   const long long n = (long long)ctx->g.V * 4;
-  k_project_u3<<<(unsigned)((n + SMEAR_BLOCK - 1) / SMEAR_BLOCK), SMEAR_BLOCK, 0, ctx->stream>>>(
-      (double2*)out, (const double2*)in, n, ctx->d_flag);
+  const unsigned nb = (unsigned)((n + SMEAR_BLOCK - 1) / SMEAR_BLOCK);
+  if (prec == HISQ_DF64)
+    k_project_u3<df64><<<nb, SMEAR_BLOCK, 0, ctx->stream>>>((double2*)out, (const double2*)in, n, ctx->d_flag);
+  else
+    k_project_u3<double><<<nb, SMEAR_BLOCK, 0, ctx->stream>>>((double2*)out, (const double2*)in, n, ctx->d_flag);
   note_launch(ctx);
   HISQ_CUDA(cudaGetLastError());
   return HISQ_OK;
@@ -565,7 +571,7 @@ extern "C" int hisq_project_u3(hisq_ctx* c, double* out, const double* in) {
   const size_t bytes = (size_t)c->g.V * 4 * 18 * sizeof(double);
   if (out != in && overlap(out, in, bytes)) return set_error(HISQ_EINVAL, "output links partly overlap the input");
   HISQ_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-  if ((rc = launch_project(c, out, in))) return rc;
+  if ((rc = launch_project(c, out, in, HISQ_F64))) return rc;
   return read_project_flag(c);
 }
 
@@ -581,7 +587,7 @@ extern "C" int hisq_hisq_links(hisq_ctx* c, double* fat, double* lng, const doub
   if (!w) return set_error(HISQ_ENOMEM, "level-1 links");
   HISQ_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
   if ((rc = smear_dispatch(c, w, nullptr, thin, *level1, prec))) return rc;
-  if ((rc = launch_project(c, w, w))) return rc;
+  if ((rc = launch_project(c, w, w, prec))) return rc;
   if ((rc = smear_dispatch(c, fat, lng, w, *level2, prec))) return rc;
   return read_project_flag(c);
 }
