@@ -135,8 +135,12 @@ int hisq_set_long_compression(hisq_ctx* ctx, double naik);
  * out = D_oe in (out_parity = 1). Vectors in precision prec (its links must be
  * resident), nrhs vectors of V/2 sites back to back; out and in must not overlap.
  * Arithmetic: FP64 for HISQ_F64, double-float for HISQ_DF64, FP32 for the others (16-bit
- * types are storage only).
- * Asynchronous on the context's stream for device pointers.
+ * types are storage only). With 16-bit storage and nrhs >= 8 there are two forms, FP32 FMAs on
+ * the CUDA cores and tensor-core products (mma.sync, FP32 accumulation). With the autotuner on,
+ * the first call per (precision, nrhs) runs and times both (the output is written twice, with
+ * equal results up to rounding order) and keeps the faster. The choice is listed by
+ * hisq_tune_report as "dslash_path/l<prec>/n<nrhs> -> 1 (CUDA cores) or 2 (tensor cores)".
+ * Asynchronous on the context's stream for device pointers (apart from that first timing call).
  * Errors: HISQ_EINVAL (parity, nrhs < 1 or > 64, precision not resident), HISQ_ENOLINKS.
  */
 int hisq_dslash(hisq_ctx* ctx, int out_parity, void* out, const void* in, int prec, int nrhs);

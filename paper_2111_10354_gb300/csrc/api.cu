@@ -81,7 +81,7 @@ static int dslash_launch_16bit_multi(hisq_ctx* ctx, int lp, const DslashCall& c)
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   HISQ_CUDA(cudaStreamIsCapturing(ctx->stream, &cap));
   if (!ctx->autotune || cap != cudaStreamCaptureStatusNone) return dslash_launch_core(ctx, lp, lp, c);
-  cudaEvent_t e[3];
+  cudaEvent_t e[2];
   for (auto& ev : e) HISQ_CUDA(cudaEventCreate(&ev));
   float ms[2] = {0.f, 0.f};
   int rc = HISQ_OK;
