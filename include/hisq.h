@@ -22,8 +22,9 @@
  *              D_eo maps odd-site vectors to even sites; D_oe maps even to odd.
  *
  * Data at the boundary:
- *   links      host, complex128 interleaved (re, im), [t][z][y][x][mu][row][col],
- *              x fastest, mu = 0..3 = x, y, z, t.
+ *   links      host or device memory, complex128 interleaved (re, im),
+ *              [t][z][y][x][mu][row][col], x fastest, mu = 0..3 = x, y, z, t (the layout
+ *              hisq_smear writes, so smeared links can be loaded straight from the device).
  *   vectors    [rhs][cb][color] over the sites of one parity, complex numbers stored
  *              as (re, im) pairs of the precision's real type: HISQ_F64 and HISQ_DF64
  *              complex128, HISQ_F32 complex64, HISQ_F16 two IEEE binary16, HISQ_BF16 two
@@ -101,10 +102,10 @@ int hisq_create(hisq_ctx** out, const int dims[4], unsigned prec_mask, void* str
 int hisq_destroy(hisq_ctx* ctx);
 
 /*
- * Load fat and long links for the whole lattice (host arrays in the link layout
- * above, V*4*9 complex128 each). flags: HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T.
+ * Load fat and long links for the whole lattice (host or device arrays in the link
+ * layout above, V*4*9 complex128 each). flags: HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T.
  * The links are folded (phases, boundary sign) and converted to every resident
- * precision on the device; the host arrays are not kept. Returns HISQ_ENONFINITE if
+ * precision on the device; the input arrays are not kept. Returns HISQ_ENONFINITE if
  * any entry is NaN or Inf (the previous links are then no longer valid).
  */
 int hisq_load_links(hisq_ctx* ctx, const double* fat, const double* lng, unsigned flags);
