@@ -774,6 +774,27 @@ def row_smear(h, torch, hin):
     by = 2 * V * 4 * 144
     print(json.dumps({"row": "smear", "lattice": lname, "what": "U(3) projection (FP64)", "ms": round(ms, 3),
                       "GB/s": round(by / (ms * 1e-3) / 1e9, 1)}), flush=True)
+    # one level at the other sizes of the Dslash sweep that fit (inputs, outputs and workspaces take
+    # 3 x 576 + 117 x 16 B per site: 96^3x24 needs 77 GB, 144^3x36 would need 387 GB)
+    del lat, U, fat, lng
+    torch.cuda.empty_cache()
+    for Ls in ((32, 32, 32, 8), (64, 64, 64, 16), (96, 96, 96, 24)):
+        Vs = int(np.prod(Ls))
+        lat_s = h.Lattice(Ls, precs=(h.HISQ_F64,), stream=stream)
+        Us = torch.from_numpy(hin.gen_thin(Ls, GAUGE_SEED, 0.3).reshape(Vs, 4, 3, 3)).cuda()
+        fs, ls = torch.empty_like(Us), torch.empty_like(Us)
+        torch.cuda.synchronize()
+        for prec, name in ((h.HISQ_F64, "f64"), (h.HISQ_DF64, "df64")):
+            ms = _stream_ms(torch, stream, lambda: lat_s.smear(fs, ls, Us, SMEAR_LEVEL2, prec), 2)
+            gf = SMEAR_FLOPS_PER_SITE * Vs / (ms * 1e-3) / 1e9
+            line = {"row": "smear", "lattice": "x".join(map(str, Ls)), "arith": name,
+                    "what": "one level, all paths + Naik", "ms": round(ms, 3), "GFLOP/s": round(gf, 1),
+                    "sites_per_s": round(Vs / (ms * 1e-3), 1)}
+            if prec == h.HISQ_F64:
+                line["frac_fp64_pipe"] = round(gf / (FP64_PIPE_TFLOPS * 1e3), 3)
+            print(json.dumps(line), flush=True)
+        del lat_s, Us, fs, ls
+        torch.cuda.empty_cache()
     # the oracle (numpy, explicit path sums) on a sample of sites
     n = 2048
     sample = np.random.default_rng(3).choice(V, n, replace=False)
