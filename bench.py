@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
     ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-df64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8",
                                                    "cg-f32-nr8", "ptc", "fcg", "batch", "smear-f64", "smear-df64",
-                                                   "dslash-f16-nr16-tc", "dslash-f16-nr16-cc"],
+                                                   "dslash-f16-nr16-tc", "dslash-f16-nr16-cc", "cg-f32", "multishift"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned", "smear"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
@@ -853,6 +853,23 @@ def run_kernel_case(name):
             x.zero_()
             torch.cuda.synchronize()
             rc, st = lat.cg(x, b, 0.01, 1e-10, 5000, nrhs=8, inner_prec=h.HISQ_F32)
+        print(json.dumps({"case": name, "iters": st["iters"], "s": round(st["seconds"], 4)}))
+    elif name in ("cg-f32", "multishift"):
+        L = (48, 48, 48, 12)
+        fat, lng = hin.gen_links(L, 1001 if name == "cg-f32" else 1002, 0.3, 0.1)
+        lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=stream).load(fat, lng)
+        b = torch.from_numpy(hin.gen_source(2001 if name == "cg-f32" else 2002, lat.half, 1)).cuda()
+        torch.cuda.synchronize()
+        for _ in range(2):  # the first solve tunes and captures, the second replays
+            if name == "cg-f32":
+                x = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                rc, st = lat.cg(x, b, 0.01, 1e-10, 5000, inner_prec=h.HISQ_F32)
+            else:
+                shifts = np.logspace(-5, 0, 14)
+                x = torch.zeros((14,) + tuple(b.shape[1:]), dtype=b.dtype, device="cuda")
+                torch.cuda.synchronize()
+                rc, st = lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 5000, inner_prec=h.HISQ_F32)
         print(json.dumps({"case": name, "iters": st["iters"], "s": round(st["seconds"], 4)}))
     elif name == "ptc":
         import oracle.ptc as optc

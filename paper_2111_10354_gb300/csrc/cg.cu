@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <type_traits>
 #include <vector>
 
 #include "solver_common.cuh"
@@ -705,20 +706,26 @@ __global__ void k_ms_rupdate(S* __restrict__ r, const S* __restrict__ Ap, size_t
   }
 }
 
-// For every active shift: x_k += alpha_k*scale*p_k; p_k = zeta_k' r + beta_k p_k (r read once).
+// For every active shift: x_k += alpha_k p_k; p_k = zeta_k' r + beta_k p_k (r read once).
+// X = double: x_k is the FP64 solution in true units (alpha_k * scale). X = float (FP32 Krylov
+// vectors): x_k is an FP32 correction in inner units, folded into the FP64 solutions once the
+// Krylov phase ends (k_ms_fold) -- two FP64 operations per entry and shift would otherwise bind this
+// streaming kernel to GB300's FP64 pipe. The FP64 verification and refinement that follow the FP32
+// Krylov phase correct what the FP32 accumulation loses.
 // Last block: commit the recurrences, freeze converged shifts, count the iteration.
-template <typename S>
-__global__ void k_ms_update(double2* __restrict__ x, S* __restrict__ p, const S* __restrict__ r, size_t n,
+template <typename S, typename X>
+__global__ void k_ms_update(X* __restrict__ x, S* __restrict__ p, const S* __restrict__ r, size_t n,
                             MsState* st, unsigned* counter) {
   if (st->done) return;
   using T = typename Real<S>::acc;
-  __shared__ double s_ax[MAXR];
+  using XT = typename Real<X>::acc;
+  __shared__ XT s_ax[MAXR];
   __shared__ T s_z[MAXR], s_b[MAXR];
   __shared__ int s_act[MAXR];
   const int ns = st->nshift;
   for (int k = threadIdx.x; k < ns; k += blockDim.x) {
     s_act[k] = st->active[k];
-    s_ax[k] = st->alpha_k[k] * st->scale;
+    s_ax[k] = XT(sizeof(X) == 8 ? st->alpha_k[k] * st->scale : st->alpha_k[k]);
     s_z[k] = T(st->zeta_new[k]);
     s_b[k] = T(st->beta_k[k]);
   }
@@ -731,17 +738,17 @@ __global__ void k_ms_update(double2* __restrict__ x, S* __restrict__ p, const S*
       if (!s_act[k]) continue;
       const size_t j = (size_t)k * n + i;
       cplx<T> pv[K];
-      cplx<double> xv[K];
+      cplx<XT> xv[K];
       Chunk<S>::load(p, j / K, pv);
-      load_k<double, K>((const double*)x, j, xv);
+      load_k<X, K>(x, j, xv);
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        xv[c].re += s_ax[k] * (double)pv[c].re;
-        xv[c].im += s_ax[k] * (double)pv[c].im;
+        xv[c].re = fma(s_ax[k], XT(pv[c].re), xv[c].re);
+        xv[c].im = fma(s_ax[k], XT(pv[c].im), xv[c].im);
         pv[c].re = fma(s_b[k], pv[c].re, s_z[k] * rv[c].re);
         pv[c].im = fma(s_b[k], pv[c].im, s_z[k] * rv[c].im);
       }
-      store_k<double, K>((double*)x, j, xv);
+      store_k<X, K>(x, j, xv);
       Chunk<S>::store(p, j / K, pv);
     }
   }
@@ -772,10 +779,10 @@ __global__ void k_ms_update(double2* __restrict__ x, S* __restrict__ p, const S*
   if (finished || st->cycle_iter >= st->cycle_limit || st->breakdown || st->nonfinite) st->done = 1;
 }
 
-// r = b / scale; p_k = r; x_k = 0.
-template <typename S>
-__global__ void k_ms_init(const double2* __restrict__ b, S* __restrict__ r, S* __restrict__ p,
-                          double2* __restrict__ x, size_t n, int ns, double inv_scale) {
+// r = b / scale; p_k = r; x_k = 0 (x: the FP64 solutions or the FP32 corrections, see k_ms_update).
+template <typename S, typename X>
+__global__ void k_ms_init(const double2* __restrict__ b, S* __restrict__ r, S* __restrict__ p, X* __restrict__ x,
+                          size_t n, int ns, double inv_scale) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double2 bv = b[i];
     const S re = S(bv.x * inv_scale), im = S(bv.y * inv_scale);
@@ -785,8 +792,18 @@ __global__ void k_ms_init(const double2* __restrict__ b, S* __restrict__ r, S* _
       const size_t j = (size_t)k * n + i;
       p[2 * j] = re;
       p[2 * j + 1] = im;
-      x[j] = make_double2(0.0, 0.0);
+      x[2 * j] = X(0);
+      x[2 * j + 1] = X(0);
     }
+  }
+}
+
+// x_k = scale * e_k for every shift: the FP32 corrections of the Krylov phase into the FP64 solutions.
+__global__ void k_ms_fold(double2* __restrict__ x, const float2* __restrict__ e, size_t total, const MsState* st) {
+  const double scale = st->scale;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = e[i];
+    x[i] = make_double2(scale * (double)v.x, scale * (double)v.y);
   }
 }
 
@@ -807,7 +824,7 @@ __global__ void k_norm2(const double2* __restrict__ b, size_t n, double* partial
 }
 
 template <typename S>
-static int ms_iteration(hisq_ctx* ctx, int lp, double2* x, S* r, S* p, S* Ap, S* t, MsState* st, double* partials,
+static int ms_iteration(hisq_ctx* ctx, int lp, void* xacc, S* r, S* p, S* Ap, S* t, MsState* st, double* partials,
                         double a_base, int base, int ns) {
   const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
   const size_t n = (size_t)ctx->g.half * 3;
@@ -834,7 +851,8 @@ static int ms_iteration(hisq_ctx* ctx, int lp, double2* x, S* r, S* p, S* Ap, S*
   if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
   const int grid = blas_grid(ctx, 1, n / Chunk<S>::K, 4).x;  // one thread per 16-byte chunk, one wave
   k_ms_rupdate<S><<<grid, 256, 0, ctx->stream>>>(r, Ap, n, st, partials, partial_stride(ctx), ctx->d_counters + 7);
-  k_ms_update<S><<<grid, 256, 0, ctx->stream>>>(x, p, r, n, st, ctx->d_counters + 8);
+  using X = typename std::conditional<sizeof(S) == 8, double, float>::type;  // see k_ms_update
+  k_ms_update<S, X><<<grid, 256, 0, ctx->stream>>>((X*)xacc, p, r, n, st, ctx->d_counters + 8);
   HISQ_CUDA(cudaGetLastError());
   note_launch(ctx, 2);
   (void)ns;
@@ -852,9 +870,12 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
   S* Ap = (S*)workspace(ctx, "ms_Ap", n * 2 * sizeof(S));
   S* t = (S*)workspace(ctx, "ms_t", n * 2 * sizeof(S));
   S* p = (S*)workspace(ctx, "ms_p", (size_t)ns * n * 2 * sizeof(S));
+  // the solutions' accumulator during the Krylov phase: x itself (FP64 vectors) or FP32 corrections
+  using X = typename std::conditional<sizeof(S) == 8, double, float>::type;
+  X* xacc = sizeof(S) == 8 ? (X*)x : (X*)workspace(ctx, "ms_e", (size_t)ns * n * 2 * sizeof(float));
   MsState* st = (MsState*)workspace(ctx, "ms_state", sizeof(MsState));
   double* partials = (double*)workspace(ctx, "ms_partials", 2 * MAXR * partial_stride(ctx) * sizeof(double));
-  if (!r || !Ap || !t || !p || !st || !partials) return set_error(HISQ_ENOMEM, "multi-shift workspace");
+  if (!r || !Ap || !t || !p || !xacc || !st || !partials) return set_error(HISQ_ENOMEM, "multi-shift workspace");
   MsState* h = (MsState*)ctx->pinned;
   int base = 0;
   for (int k = 1; k < ns; ++k)
@@ -890,7 +911,7 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
     h->tol2[k] = tol[k] * tol[k] * bb;
   }
   HISQ_CUDA(cudaMemcpyAsync(st, h, sizeof(MsState), cudaMemcpyHostToDevice, ctx->stream));
-  k_ms_init<S><<<grid1, 256, 0, ctx->stream>>>(b, r, p, x, n, ns, 1.0 / scale);
+  k_ms_init<S, X><<<grid1, 256, 0, ctx->stream>>>(b, r, p, xacc, n, ns, 1.0 / scale);
   HISQ_CUDA(cudaGetLastError());
   note_launch(ctx);
   const double a_base = 4.0 * mass * mass + shifts[base];
@@ -901,8 +922,8 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
     std::string key = "ms/" + std::to_string(sizeof(S)) + "/" + std::to_string(lp) + "/" + std::to_string(ns) + "/" +
                       std::to_string(base) + "/" + std::to_string(cycle);
     char buf[64];
-    for (const void* ptr : {(const void*)x, (const void*)r, (const void*)p, (const void*)Ap, (const void*)t,
-                            (const void*)st, (const void*)partials}) {
+    for (const void* ptr : {(const void*)x, (const void*)xacc, (const void*)r, (const void*)p, (const void*)Ap,
+                            (const void*)t, (const void*)st, (const void*)partials}) {
       snprintf(buf, sizeof buf, "/%p", ptr);
       key += buf;
     }
@@ -939,7 +960,7 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
       ctx->capturing = true;
       int crc = HISQ_OK;
       for (int i = 0; i < cycle && crc == HISQ_OK; ++i)
-        crc = ms_iteration<S>(ctx, lp, x, r, p, Ap, t, st, partials, a_base, base, ns);
+        crc = ms_iteration<S>(ctx, lp, xacc, r, p, Ap, t, st, partials, a_base, base, ns);
       ctx->capturing = false;
       cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
       if (crc != HISQ_OK) return crc;
@@ -964,7 +985,7 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
       ctx->launches += graph_nodes;
     } else {
       for (int i = 0; i < cycle; ++i) {
-        int rc = ms_iteration<S>(ctx, lp, x, r, p, Ap, t, st, partials, a_base, base, ns);
+        int rc = ms_iteration<S>(ctx, lp, xacc, r, p, Ap, t, st, partials, a_base, base, ns);
         if (rc != HISQ_OK) return rc;
       }
     }
@@ -987,6 +1008,11 @@ static int run_multishift(hisq_ctx* ctx, double2* x, const double2* b, int ns, c
     h->cycle_iter = 0;
     HISQ_CUDA(cudaMemcpyAsync(&st->done, &h->done, 2 * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  if (sizeof(S) != 8) {  // the FP32 corrections into the FP64 solutions (also on the error paths)
+    k_ms_fold<<<grid1, 256, 0, ctx->stream>>>(x, (const float2*)xacc, (size_t)ns * n, st);
+    HISQ_CUDA(cudaGetLastError());
+    note_launch(ctx);
   }
   if (stats) {
     for (int k = 0; k < ns; ++k) stats->shift_iters[k] = h->conv_iter[k];
