@@ -595,14 +595,17 @@ def row_multishift(h, torch, hin):
     """48^3x12, m = 0.0025, 14 shifts log-spaced in [1e-5, 1], every shift to 1e-9."""
     L = (48, 48, 48, 12)
     fat, lng = hin.gen_links(L, 1002, 0.3, 0.1)
-    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=torch.cuda.Stream()).load(fat, lng)
+    lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_DF64), stream=torch.cuda.Stream()).load(fat, lng)
     shifts = np.logspace(-5, 0, 14)
     b = torch.from_numpy(hin.gen_source(2002, lat.half, 1)).cuda()
     x = torch.zeros((14, lat.half, 3), dtype=torch.complex128, device="cuda")
     torch.cuda.synchronize()  # inputs come from torch's stream, the solve runs on the library's
-    for name, prec in (("fp32_krylov+refine", h.HISQ_F32), ("fp64", h.HISQ_F64)):
-        lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 20000, inner_prec=prec)
-        dt, (rc, st) = _timed(torch, lambda: lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 20000, inner_prec=prec))
+    for name, o in (("fp32_krylov+refine", dict(inner_prec=h.HISQ_F32)),
+                    ("fp32_krylov+refine, df64 verification and reliable updates",
+                     dict(inner_prec=h.HISQ_F32, reliable_prec=h.HISQ_DF64)),
+                    ("fp64", dict(inner_prec=h.HISQ_F64))):
+        lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 20000, **o)
+        dt, (rc, st) = _timed(torch, lambda: lat.multishift_cg(x, b, shifts, 0.0025, 1e-9, 20000, **o))
         print(json.dumps({"row": "multishift", "variant": name, "s": round(dt, 4), "iters": st["iters"],
                           "shift_iters": st["shift_iters"], "max_true_res": max(st["shift_residual"]),
                           "converged": st["converged"], "kernel_launches": st["kernel_launches"]}), flush=True)
