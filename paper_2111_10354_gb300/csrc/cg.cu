@@ -200,8 +200,12 @@ __global__ void __launch_bounds__(256, 6) k_update(X* __restrict__ x, S* __restr
   // X = double: x is the solution itself, in true units (alpha * scale); X = float: e is in
   // inner units and k_fold applies the scale
   const XT ax = XT(sizeof(X) == 8 ? alpha * st->scale[rh] : alpha);
-  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < n; i += (size_t)gridDim.x * blockDim.x * K) {
-    if (st->rhs_done[rh]) break;  // frozen rhs: its vectors are not touched (uniform per block)
+  // a frozen rhs's vectors are not touched; the flag is read once (it only changes between launches),
+  // so no load of it sits in front of every iteration's vector loads
+  const bool frozen = st->rhs_done[rh];
+#pragma unroll 2
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < (frozen ? 0 : n);
+       i += (size_t)gridDim.x * blockDim.x * K) {
     cplx<T> pv[K], rv[K], av[K];
     Chunk<S>::load(p, (off + i) / K, pv);
     Chunk<S>::load(r, (off + i) / K, rv);
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(256, 8) k_pupdate(const S* __restrict__ r, S* 
   const size_t off = (size_t)rh * n;
   if (!st->rhs_done[rh]) {
     const T beta = T(st->rr_new[rh] / st->rr[rh]);
+#pragma unroll 2
     for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < n;
          i += (size_t)gridDim.x * blockDim.x * K) {
       cplx<T> pv[K], rv[K];
@@ -678,18 +683,24 @@ __global__ void k_ms_rupdate(S* __restrict__ r, const S* __restrict__ Ap, size_t
     v += (double)t;
   }
   __shared__ double red[32];
+  __shared__ double s_tot;
   double s = block_sum_dyn(v, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
   if (!last_block_done(counter)) return;
   double tot = sum_partials_dyn(partials, gridDim.x, red);
-  if (threadIdx.x != 0) return;
-  if (!(pap > 0.0)) st->breakdown = 1;
-  if (!isfinite(tot)) st->nonfinite = 1;
-  st->rr_new = tot;
-  st->alpha = alpha;
-  const double beta = tot / st->rr;
+  if (threadIdx.x == 0) {
+    s_tot = tot;
+    if (!(pap > 0.0)) st->breakdown = 1;
+    if (!isfinite(tot)) st->nonfinite = 1;
+    st->rr_new = tot;
+    st->alpha = alpha;
+  }
+  __syncthreads();
+  // the shifts' recurrences are independent: one thread each (GB300's FP64 divisions are slow in a
+  // single thread's dependent chain)
+  const double beta = s_tot / st->rr;
   const double s0 = st->sigma[st->base];
-  for (int k = 0; k < st->nshift; ++k) {
+  for (int k = threadIdx.x; k < st->nshift; k += blockDim.x) {
     if (!st->active[k]) continue;
     double zn;
     if (k == st->base) {
