@@ -169,17 +169,6 @@ __device__ __forceinline__ void mul_nn_acc(M3<T>& acc, const M3<T>& a, const M3<
       for (int k = 0; k < 3; ++k) cmac(acc.e[3 * i + j], a.e[3 * i + k], b.e[3 * k + j]);
 }
 
-// acc += a b^dag
-template <typename T>
-__device__ __forceinline__ void mul_nd_acc(M3<T>& acc, const M3<T>& a, const M3<T>& b) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cmac(acc.e[3 * i + j], a.e[3 * i + k], conj_c(b.e[3 * j + k]));
-}
-
 template <typename T>
 __device__ __forceinline__ void scale_m(M3<T>& m, T c) {
   const T z = FieldIO<T>::zero();
