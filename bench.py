@@ -778,7 +778,7 @@ def row_smear(h, torch, hin):
     print(json.dumps({"row": "smear", "lattice": lname, "what": "U(3) projection (FP64)", "ms": round(ms, 3),
                       "GB/s": round(by / (ms * 1e-3) / 1e9, 1)}), flush=True)
     # one level at the other sizes of the Dslash sweep that fit (inputs, outputs and workspaces take
-    # 3 x 576 + 117 x 16 B per site: 96^3x24 needs 77 GB, 144^3x36 would need 387 GB)
+    # 3 x 576 + 144 x 16 B per site: 96^3x24 needs 86 GB, 144^3x36 would need 433 GB)
     del lat, U, fat, lng
     torch.cuda.empty_cache()
     for Ls in ((32, 32, 32, 8), (64, 64, 64, 16), (96, 96, 96, 24)):

@@ -343,7 +343,7 @@ typedef struct {
  * outputs can be passed to hisq_load_links directly). lng may be NULL (long links not formed).
  * Outputs must not overlap the input or each other. prec: the arithmetic, HISQ_F64 (IEEE FP64) or
  * HISQ_DF64 (double-float on the FP32 pipe, ~2^-47 relative rounding per operation); inputs and
- * outputs are binary64 either way. Uses 117 * 16 bytes of context workspace per site. Stream-ordered,
+ * outputs are binary64 either way. Uses 144 * 16 bytes of context workspace per site. Stream-ordered,
  * no host synchronisation. Errors: HISQ_EINVAL (null or host pointer, misaligned, overlapping,
  * non-finite coefficient, other prec), HISQ_ENOMEM, HISQ_ECUDA.
  */

@@ -5,8 +5,9 @@
 //
 // One level, for each direction mu, runs three passes over the whole lattice (lexicographic sites)
 // whose intermediates stay in HBM:
-//   pass 1  S_{nu,s}(x): the staple of U_mu in direction s*nu, for the 3 transverse nu and s = +-
-//   pass 2  Y_a(x) = c3 U_mu(x) + sum_{b != a} sum_r staple_{b,r}[c5 U_mu + c7 (S_{c,+} + S_{c,-})](x),
+//   pass 1  S_{nu,s}(x): the staple of U_mu in direction s*nu, for the 3 transverse nu and s = +-,
+//           and X_nu(x) = c5 U_mu(x) + c7 (S_{nu,+}(x) + S_{nu,-}(x))
+//   pass 2  Y_a(x) = c3 U_mu(x) + sum_{b != a} sum_r staple_{b,r}[X_c](x),
 //           c the transverse direction other than a and b
 //   pass 3  F_mu(x) = c1 U_mu(x) + sum_a sum_r staple_{a,r}[Y_a + cL S_{a,r}](x)
 //           L_mu(x) = cN U_mu(x) U_mu(x+mu) U_mu(x+2mu)
@@ -55,6 +56,10 @@ struct FieldIO<double> {
     const long long m = c ? (long long)0x8000000000000000ull : 0ll;
     return {v.x, __longlong_as_double(__double_as_longlong(v.y) ^ m)};
   }
+  __device__ __forceinline__ static cplx<double> ld_coherent(const S* p) {  // written by this kernel
+    const S v = *p;
+    return {v.x, v.y};
+  }
   __device__ __forceinline__ static void st(S* p, const cplx<double>& c) { *p = make_double2(c.re, c.im); }
   __device__ __forceinline__ static cplx<double> from_f64(double2 v) { return {v.x, v.y}; }
   __device__ __forceinline__ static double2 to_f64(const cplx<double>& c) { return make_double2(c.re, c.im); }
@@ -72,6 +77,10 @@ struct FieldIO<df64> {
     const S v = __ldg(p);
     const unsigned m = c ? 0x80000000u : 0u;
     return {df64(v.x, v.y), df64(__uint_as_float(__float_as_uint(v.z) ^ m), __uint_as_float(__float_as_uint(v.w) ^ m))};
+  }
+  __device__ __forceinline__ static cplx<df64> ld_coherent(const S* p) {  // written by this kernel
+    const S v = *p;
+    return {df64(v.x, v.y), df64(v.z, v.w)};
   }
   __device__ __forceinline__ static void st(S* p, const cplx<df64>& c) {
     *p = make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo);
@@ -218,11 +227,13 @@ __global__ void __launch_bounds__(SMEAR_BLOCK) k_to_fields(const double2* __rest
 // inside the instruction cache.
 
 // Pass 1: the six one-signed staples of U_mu at every site, S_{nu,+} at field 2j, S_{nu,-} at 2j+1
-// (nu = transverse(mu, j)).
+// (nu = transverse(mu, j)), and the middle field of pass 2 for each transverse direction,
+// X_j = c5 U_mu + c7 (S_{nu,+} + S_{nu,-}), at field j of Xf.
 template <typename T, int MINB>
 __global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_staples(const typename FieldIO<T>::S* __restrict__ U,
-                                                               typename FieldIO<T>::S* __restrict__ St, Geom g,
-                                                               int mu) {
+                                                               typename FieldIO<T>::S* __restrict__ St,
+                                                               typename FieldIO<T>::S* __restrict__ Xf, Geom g,
+                                                               int mu, double c5, double c7) {
   using S = typename FieldIO<T>::S;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
@@ -245,6 +256,20 @@ __global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_staples(const t
     zero_m(r);
     mul_nn_acc(r, p, a);
     store_m(St + (size_t)it * 9 * V, V, s, r);
+    if (bwd) {  // r = S_{nu,-}; S_{nu,+} was stored by this thread one iteration ago
+      const S* Sp = St + (size_t)(it - 1) * 9 * V;
+      S* Xj = Xf + (size_t)(it >> 1) * 9 * V;
+      const T t5 = FieldIO<T>::coef(c5), t7 = FieldIO<T>::coef(c7), z = FieldIO<T>::zero();
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const cplx<T> u = FieldIO<T>::ld(Umu + (size_t)k * V + s);
+        const cplx<T> sp = FieldIO<T>::ld_coherent(Sp + (size_t)k * V + s);
+        cplx<T> x;
+        x.re = fma(t7, sp.re + r.e[k].re, fma(t5, u.re, z));
+        x.im = fma(t7, sp.im + r.e[k].im, fma(t5, u.im, z));
+        FieldIO<T>::st(Xj + (size_t)k * V + s, x);
+      }
+    }
   }
 }
 
@@ -252,9 +277,9 @@ __global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_staples(const t
 // are neighbouring blocks, so the links and staples of a group of sites are read while in L2.
 template <typename T, int MINB>
 __global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_middle(const typename FieldIO<T>::S* __restrict__ U,
-                                                              const typename FieldIO<T>::S* __restrict__ St,
+                                                              const typename FieldIO<T>::S* __restrict__ Xf,
                                                               typename FieldIO<T>::S* __restrict__ Y, Geom g, int mu,
-                                                              double c3, double c5, double c7) {
+                                                              double c3) {
   using S = typename FieldIO<T>::S;
   const int ai = blockIdx.x % 3;
   const int s = (blockIdx.x / 3) * blockDim.x + threadIdx.x;
@@ -263,7 +288,6 @@ __global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_middle(const ty
   int c[4];
   lex_coords(g, s, c);
   const S* Umu = U + (size_t)mu * 9 * V;
-  const T t5 = FieldIO<T>::coef(c5), t7 = FieldIO<T>::coef(c7);
   M3<T> y;
   load_m(y, Umu, V, s, false);
   scale_m(y, FieldIO<T>::coef(c3));
@@ -274,11 +298,10 @@ __global__ void __launch_bounds__(SMEAR_MAX_BLOCK, MINB) k_smear_middle(const ty
     const int b = transverse(mu, bi);
     const S* Ub = U + (size_t)b * 9 * V;
     // forward: U_b(x) X(x+b) U_b(x+mu)^dag; backward: U_b(x-b)^dag X(x-b) U_b(x-b+mu);
-    // X = c5 U_mu + c7 (S_{c,+} + S_{c,-})
+    // X = c5 U_mu + c7 (S_{c,+} + S_{c,-}), formed by pass 1
     const int y0 = bwd ? step(g, s, c[b], b, -1) : s;
     M3<T> x, u, p;
-    load_comb(x, Umu, t5, St + (size_t)(2 * ci) * 9 * V, St + (size_t)(2 * ci + 1) * 9 * V, t7, V,
-              bwd ? y0 : step(g, s, c[b], b, 1));
+    load_m(x, Xf + (size_t)ci * 9 * V, V, bwd ? y0 : step(g, s, c[b], b, 1), false);
     load_m(u, Ub, V, y0, bwd);
     mul_nn(p, u, x);
     load_m(u, Ub, V, step(g, y0, c[mu], mu, 1), !bwd);
@@ -454,7 +477,8 @@ int smear_level(hisq_ctx* ctx, double* fat, double* lng, const double* thin, con
   S* U = (S*)workspace(ctx, "smear_thin", 36 * V * sizeof(S));
   S* Sf = (S*)workspace(ctx, "smear_staples", 54 * V * sizeof(S));
   S* Y = (S*)workspace(ctx, "smear_middle", 27 * V * sizeof(S));
-  if (!U || !Sf || !Y) return set_error(HISQ_ENOMEM, "smearing workspaces (%zu bytes)", 117 * V * sizeof(S));
+  S* Xf = (S*)workspace(ctx, "smear_x", 27 * V * sizeof(S));
+  if (!U || !Sf || !Y || !Xf) return set_error(HISQ_ENOMEM, "smearing workspaces (%zu bytes)", 144 * V * sizeof(S));
   k_to_fields<T><<<dim3(blocks_for(V, SMEAR_BLOCK), 36), SMEAR_BLOCK, 0, st>>>((const double2*)thin, U, g.V);
   HISQ_CUDA(cudaGetLastError());
   note_launch(ctx);
@@ -465,13 +489,13 @@ int smear_level(hisq_ctx* ctx, double* fat, double* lng, const double* thin, con
   for (int mu = 0; mu < 4; ++mu) {
     int rc = launch_pass(ctx, dd ? "smear/staples/df64" : "smear/staples/f64", k_smear_staples<T, 1>,
                          k_smear_staples<T, 2>, [&](decltype(&k_smear_staples<T, 1>) k, int b) {
-                           k<<<blocks_for(V, b), b, 0, st>>>(U, Sf, g, mu);
+                           k<<<blocks_for(V, b), b, 0, st>>>(U, Sf, Xf, g, mu, c5, c7);
                            return cudaGetLastError();
                          });
     if (rc) return rc;
     rc = launch_pass(ctx, dd ? "smear/middle/df64" : "smear/middle/f64", k_smear_middle<T, 1>, k_smear_middle<T, 2>,
                      [&](decltype(&k_smear_middle<T, 1>) k, int b) {
-                       k<<<3 * blocks_for(V, b), b, 0, st>>>(U, Sf, Y, g, mu, c3, c5, c7);
+                       k<<<3 * blocks_for(V, b), b, 0, st>>>(U, Xf, Y, g, mu, c3);
                        return cudaGetLastError();
                      });
     if (rc) return rc;
