@@ -366,6 +366,14 @@ int hisq_project_u3(hisq_ctx* ctx, double* out, const double* in);
 int hisq_hisq_links(hisq_ctx* ctx, double* fat, double* lng, const double* thin, const hisq_smear_coeffs* level1,
                     const hisq_smear_coeffs* level2, int prec);
 
+/*
+ * Free the context's device workspaces (staging buffers, solver and smearing scratch) and the solver
+ * graphs cached on them; both are allocated again on demand by the next call that needs them.
+ * Synchronises the stream first. Link storage and the autotuner's cache are kept. Errors:
+ * HISQ_EINVAL (null context), HISQ_ECUDA.
+ */
+int hisq_release_workspaces(hisq_ctx* ctx);
+
 /* ---------------------------------------------------------------- diagnostics */
 const char* hisq_strerror(int code);
 const char* hisq_last_error(void);

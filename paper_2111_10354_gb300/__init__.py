@@ -111,6 +111,7 @@ def _load():
     lib.hisq_tune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.hisq_tune_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
     lib.hisq_selftest_bounded_wait.argtypes = [vp]
+    lib.hisq_release_workspaces.argtypes = [vp]
     cp = ctypes.POINTER(hisq_smear_coeffs)
     lib.hisq_smear.argtypes = [vp, vp, vp, vp, cp, ip]
     lib.hisq_project_u3.argtypes = [vp, vp, vp]
@@ -335,6 +336,10 @@ def hisq_hisq_links(ctx, fat, lng, thin, level1, level2, prec: int = HISQ_F64):
     c1, c2 = _coeffs(level1), _coeffs(level2)
     _check(_load().hisq_hisq_links(ctx, _ptr(fat), _ptr(lng), _ptr(thin), ctypes.byref(c1), ctypes.byref(c2), prec),
            "hisq_hisq_links")
+
+
+def hisq_release_workspaces(ctx):
+    _check(_load().hisq_release_workspaces(ctx), "hisq_release_workspaces")
 
 
 def hisq_selftest_bounded_wait(ctx) -> int:

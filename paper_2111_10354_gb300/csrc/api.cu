@@ -539,6 +539,16 @@ int hisq_tune_load(hisq_ctx* c, const char* report, int* loaded) {
   return HISQ_OK;
 }
 
+int hisq_release_workspaces(hisq_ctx* c) {
+  if (!c) return set_error(HISQ_EINVAL, "null context");
+  HISQ_CUDA(cudaStreamSynchronize(c->stream));
+  release_graphs(c);  // they were captured on workspace pointers
+  for (auto& kv : c->ws) cudaFree(kv.second.ptr);
+  c->ws.clear();
+  HISQ_CUDA(cudaGetLastError());
+  return HISQ_OK;
+}
+
 int hisq_tune_report(const hisq_ctx* c, char* buf, size_t len) {
   if (!c || !buf || len == 0) return set_error(HISQ_EINVAL, "null argument");
   size_t used = 0;

@@ -62,3 +62,40 @@ def test_tune_cache_report_and_load(hisq):
     ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
     ref = oracle.dslash(L, ff, lf, 0, x.cpu().numpy().astype(np.complex128)[0])
     assert rel_err(y3.cpu().numpy()[0].astype(np.complex128), ref) <= 2e-6
+
+
+def test_release_workspaces(hisq):
+    """Freeing the workspaces returns their memory to the device; smearing and a graph-captured solve
+    then allocate and capture again and still match the oracle."""
+    import torch
+    from oracle import smear as sm
+    L = (16, 16, 16, 16)
+    V = int(np.prod(L))
+    U = hin.gen_thin(L, 90, 0.3).reshape(V, 4, 3, 3)
+    fat, lng = hin.gen_links(L, 91, 0.3, 0.1)
+    lat = hisq.Lattice(L, precs=(0, 1)).load(fat, lng)
+    u = torch.from_numpy(U).cuda()
+    f, l = torch.empty_like(u), torch.empty_like(u)
+    coeffs = dict(c1=0.3, c3=0.1, c5=0.02, c7=0.004, cL=-0.05, cN=-0.2)
+    lat.smear(f, l, u, coeffs)
+    b = torch.from_numpy(hin.gen_source(92, lat.half, 1)).cuda()
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    lat.cg(x, b, 0.05, 1e-10, 2000, inner_prec=1)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    hisq.hisq_release_workspaces(lat.ctx)
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 - free0 >= 144 * 16 * V  # at least the smearing scratch
+    f.zero_()
+    lat.smear(f, l, u, coeffs)
+    torch.cuda.synchronize()
+    sample = np.arange(0, V, 97)
+    F, _ = sm.smear(L, U, **coeffs, sites=sample)
+    assert rel_err(f.cpu().numpy()[sample], F) <= 1e-12
+    x.zero_()
+    rc, st = lat.cg(x, b, 0.05, 1e-10, 2000, inner_prec=1)
+    ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
+    assert oracle.true_residual(L, ff, lf, 0.05, b.cpu().numpy()[0], x.cpu().numpy()[0]) <= 1.1e-10
+    with pytest.raises(hisq.HisqError):
+        hisq.hisq_release_workspaces(None)
