@@ -12,7 +12,7 @@ time) -- the whole-job throughput of the step -- with the roofline of the domina
 (the FP32 Dslash, timed live with CUDA events on its stream) against the measured HBM peak,
 and CG time-to-1e-10 of the mixed-precision and plain FP64 solves at m = 0.01 and 0.002.
 
---impl reference runs the CPU FP64 oracle (the reference arm of this build) on a bounded
+--impl reference runs the CPU FP64 oracle (the reference arm: there is no reference code) on a bounded
 sample of the same workload. N > 1 GPUs run independent replicas (the path is not sharded).
 """
 from __future__ import annotations

@@ -1,8 +1,8 @@
 """ORACLE -- test infrastructure only. Parallel-transport convolution (PTC) layers and the linear
 PTC preconditioner network, plus their gradients, in plain numpy FP64.
 
-The paper has no learned preconditioner; this is the project's extension of its CG (the north-star
-"learned preconditioner" line). The layer follows the gauge-equivariant parallel-transport
+The paper has no learned preconditioner; this is the project's extension of its CG with a learned
+preconditioner for a flexible CG. The layer follows the gauge-equivariant parallel-transport
 convolutions of Lehner & Wettig (2023), read as:
     psi'_a(x) = sum_b sum_h W[a, b, h] (T_h psi_b)(x),   h in {0, +mu, -mu}, mu = 0..3   (9 hops)
     T_0 psi(x)   = psi(x)
