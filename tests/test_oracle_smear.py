@@ -164,3 +164,21 @@ def test_two_level_unit_links():
     F, Lg = sm.smear(L, W, **RANDOM)
     total = RANDOM["c1"] + 6 * RANDOM["c3"] + 24 * RANDOM["c5"] + 48 * RANDOM["c7"] + 6 * RANDOM["cL"]
     np.testing.assert_allclose(F, total * U, atol=1e-14)
+
+
+def test_two_levels_gauge_covariant():
+    """Each level and the U(3) projection are covariant (W -> O W O'^dag gives W (W^dag W)^(-1/2) ->
+    O [W (W^dag W)^(-1/2)] O'^dag), so the HISQ fat and long links transform like single links."""
+    L = (4, 6, 4, 6)
+    V = volume(L)
+    U = hin.gen_thin(L, 31, 0.4).reshape(V, 4, 3, 3)
+    Om = hin.gen_gauge_xform(L, 32)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Ug[:, mu] = Om @ U[:, mu] @ dag(Om[shift(L, mu, 1)])
+    level2 = dict(c1=5 / 8, c3=1 / 16, c5=1 / 64, c7=1 / 384, cL=-1 / 16, cN=-1 / 24)
+    F, Lg = sm.hisq_links(L, U, FAT7, level2)
+    Fg, Lgg = sm.hisq_links(L, Ug, FAT7, level2)
+    for mu in range(4):
+        np.testing.assert_allclose(Fg[:, mu], Om @ F[:, mu] @ dag(Om[shift(L, mu, 1)]), atol=1e-12)
+        np.testing.assert_allclose(Lgg[:, mu], Om @ Lg[:, mu] @ dag(Om[shift(L, mu, 3)]), atol=1e-12)
