@@ -37,7 +37,8 @@ def scratch(tmp_path_factory):
         shutil.copytree(os.path.join(ROOT, sub), os.path.join(d, sub),
                         ignore=shutil.ignore_patterns("liboracle.so", "__pycache__", "*.tmp*"))
     os.makedirs(os.path.join(d, "tests"))
-    for f in ("conftest.py", "test_oracle_dslash.py", "test_oracle_solvers.py", "test_oracle_smear.py"):
+    for f in ("conftest.py", "test_oracle_dslash.py", "test_oracle_solvers.py", "test_oracle_smear.py",
+              "test_oracle_ptc.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(d, "tests", f))
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(d, "tests", "golden"))
     return str(d)
@@ -98,6 +99,37 @@ def test_smear_mutation_is_caught(scratch, name, old, new):
         f.write(original.replace(old, new, 1))
     try:
         rc, out = run_pins(scratch, "tests/test_oracle_smear.py")
+        assert rc != 0, "pins did not catch: " + name
+    finally:
+        with open(src_path, "w") as f:
+            f.write(original)
+
+
+PTC_MUTATIONS = [
+    ("backward transport without the conjugate", 'return np.einsum("nji,nj->ni", fat[n, mu].conj(), psi[n])',
+     'return np.einsum("nji,nj->ni", fat[n, mu], psi[n])'),
+    ("forward transport from the backward neighbour", "n = neighbours(L, mu, +1)", "n = neighbours(L, mu, -1)"),
+    ("adjoint transport taken as the transport itself", "return transport(L, fat, psi, h + 4 if h <= 4 else h - 4)",
+     "return transport(L, fat, psi, h)"),
+    ("weight gradient without the conjugate input", 'gW = np.einsum("bhvc,avc->abh", u.conj(), g_out)',
+     'gW = np.einsum("bhvc,avc->abh", u, g_out)'),
+    ("input gradient without the conjugate weights", 'mixed = np.einsum("abh,avc->bhvc", W.conj(), g_out)',
+     'mixed = np.einsum("abh,avc->bhvc", W, g_out)'),
+    ("loss gradient not averaged over pairs", "g2 = to_full(L, even=e / nx / n)[None]", "g2 = to_full(L, even=e / nx)[None]"),
+    ("tied layer 2 without the conjugate", "W2[0, a, h] = np.conj(W1[a, 0, adjoint_hop(h)])",
+     "W2[0, a, h] = W1[a, 0, adjoint_hop(h)]"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", PTC_MUTATIONS, ids=[m[0] for m in PTC_MUTATIONS])
+def test_ptc_mutation_is_caught(scratch, name, old, new):
+    src_path = os.path.join(scratch, "oracle", "ptc.py")
+    original = open(os.path.join(ROOT, "oracle", "ptc.py")).read()
+    assert old in original, "mutation anchor missing: " + old
+    with open(src_path, "w") as f:
+        f.write(original.replace(old, new, 1))
+    try:
+        rc, out = run_pins(scratch, "tests/test_oracle_ptc.py")
         assert rc != 0, "pins did not catch: " + name
     finally:
         with open(src_path, "w") as f:
