@@ -168,6 +168,25 @@ def omp_threads(n=None):
     return int(gomp.omp_get_max_threads())
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU-baseline record."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def oracle_sample(fat, lng, b, target_s: float = 12.0):
     """The oracle's FP64 CG on the same lattice, bounded: enough iterations for ~target_s seconds.
     Returns (GB/s of Dslash algorithmic bytes at FP64, seconds, iterations, threads)."""
@@ -227,6 +246,7 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(), "lattice": list(DIMS), "mass": MASS},
             "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -438,7 +458,7 @@ def run_ours(args, rank, world, local):
         # the oracle's FP64 CG on the same source, to a 1e-12 relative residual: the timed baseline, and
         # the solution each GPU solve at this mass is compared with (final error per solve)
         gbs, dt, it, threads, x_or = oracle_solve(fat, lng, b_np)
-        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": "oracle FP64 CG on 48x48x48x12 m=%g to a 1e-12 relative residual: %d iterations "
                          "(%d Dslash) in %.1f s" % (MASS, it, 2 * (it + 1), dt)}
         if x_or is not None:
