@@ -84,21 +84,32 @@ static int dslash_launch_16bit_multi(hisq_ctx* ctx, int lp, const DslashCall& c)
   cudaEvent_t e[2];
   for (auto& ev : e) HISQ_CUDA(cudaEventCreate(&ev));
   float ms[2] = {0.f, 0.f};
+  bool ok[2] = {false, false};
   int rc = HISQ_OK;
-  for (int path = 0; path < 2 && rc == HISQ_OK; ++path) {
+  for (int path = 0; path < 2; ++path) {
     auto run = [&]() { return path == 1 ? dslash_mma_launch(ctx, lp, c) : dslash_launch_core(ctx, lp, lp, c); };
     rc = run();  // tunes this form's launch shape
-    if (rc != HISQ_OK) break;
-    cudaEventRecord(e[0], ctx->stream);
-    rc = run();
-    cudaEventRecord(e[1], ctx->stream);
-    if (rc == HISQ_OK && cudaEventSynchronize(e[1]) == cudaSuccess) cudaEventElapsedTime(&ms[path], e[0], e[1]);
+    if (rc == HISQ_OK) {
+      cudaEventRecord(e[0], ctx->stream);
+      rc = run();
+      cudaEventRecord(e[1], ctx->stream);
+    }
+    if (rc == HISQ_OK && cudaEventSynchronize(e[1]) == cudaSuccess) {
+      cudaEventElapsedTime(&ms[path], e[0], e[1]);
+      ok[path] = true;
+    }
+    if (!ok[path]) {
+      if (path == 0) break;  // the CUDA-core form failed: report it
+      cudaGetLastError();    // the tensor-core form could not run here: keep the CUDA-core one
+    }
   }
   for (auto& ev : e) cudaEventDestroy(ev);
-  if (rc != HISQ_OK) return rc;
-  HISQ_CUDA(cudaGetLastError());
-  ctx->tune[key] = ms[1] < ms[0] ? 2 : 1;
-  return HISQ_OK;  // the output holds the last (tensor-core) form's result, equal to the other's
+  if (!ok[0]) return rc != HISQ_OK ? rc : set_error(HISQ_ECUDA, "Dslash timing failed");
+  const bool tensor = ok[1] && ms[1] < ms[0];
+  ctx->tune[key] = tensor ? 2 : 1;
+  // the output holds the last successful form's result (both forms agree up to rounding order)
+  if (!ok[1]) return dslash_launch_core(ctx, lp, lp, c);
+  return HISQ_OK;
 }
 
 int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
