@@ -178,6 +178,57 @@ __device__ __forceinline__ void mul_nn_acc(M3<T>& acc, const M3<T>& a, const M3<
       for (int k = 0; k < 3; ++k) cmac(acc.e[3 * i + j], a.e[3 * i + k], b.e[3 * k + j]);
 }
 
+// Double-float 3x3 products with lazy renormalisation: each product of two double-float numbers is
+// split exactly into the FP32 product of the high words and an error term (its FMA residual plus the
+// two cross terms); the high parts of an output entry's terms are summed with error-free additions
+// (Knuth's two-sum), all error terms in plain FP32, and the entry is renormalised once at the end
+// instead of after every multiply-add. The real and imaginary parts run in the two lanes of the
+// two-wide FP32 instructions.
+__device__ __forceinline__ void df_dot_term(float2& S, float2& Lo, float2 ahi, float2 alo, float2 bhi, float2 blo) {
+  const float2 p = __fmul2_rn(ahi, bhi);
+  float2 e = __ffma2_rn(ahi, bhi, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(ahi, blo, e);
+  e = __ffma2_rn(alo, bhi, e);
+  const df64x2 t = df2_two_sum(S, p);
+  S = t.hi;
+  Lo = __fadd2_rn(Lo, __fadd2_rn(t.lo, e));
+}
+
+// (S, Lo) += x y for complex x, y: (re, im) lanes += (x.re, x.re)(y.re, y.im) + (-x.im, x.im)(y.im, y.re)
+__device__ __forceinline__ void df_cmac_lazy(float2& S, float2& Lo, const cplx<df64>& x, const cplx<df64>& y) {
+  df_dot_term(S, Lo, make_float2(x.re.hi, x.re.hi), make_float2(x.re.lo, x.re.lo), make_float2(y.re.hi, y.im.hi),
+              make_float2(y.re.lo, y.im.lo));
+  df_dot_term(S, Lo, make_float2(-x.im.hi, x.im.hi), make_float2(-x.im.lo, x.im.lo), make_float2(y.im.hi, y.re.hi),
+              make_float2(y.im.lo, y.re.lo));
+}
+
+__device__ __forceinline__ void mul_nn_acc(M3<df64>& acc, const M3<df64>& a, const M3<df64>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cplx<df64>& c = acc.e[3 * i + j];
+      float2 S = make_float2(c.re.hi, c.im.hi), Lo = make_float2(c.re.lo, c.im.lo);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) df_cmac_lazy(S, Lo, a.e[3 * i + k], b.e[3 * k + j]);
+      const df64x2 r = df2_fast_two_sum(S, Lo);
+      c = {df64(r.hi.x, r.lo.x), df64(r.hi.y, r.lo.y)};
+    }
+}
+
+__device__ __forceinline__ void mul_nn(M3<df64>& c, const M3<df64>& a, const M3<df64>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float2 S = make_float2(0.f, 0.f), Lo = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) df_cmac_lazy(S, Lo, a.e[3 * i + k], b.e[3 * k + j]);
+      const df64x2 r = df2_fast_two_sum(S, Lo);
+      c.e[3 * i + j] = {df64(r.hi.x, r.lo.x), df64(r.hi.y, r.lo.y)};
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void scale_m(M3<T>& m, T c) {
   const T z = FieldIO<T>::zero();
