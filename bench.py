@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -72,12 +73,20 @@ def peaks():
         return FALLBACK_HBM, "of fallback"
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and blank lines (an edit to a comment compiles to the same kernel)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", l).rstrip() for l in text.splitlines())
+    return "\n".join(l for l in lines if l.strip())
+
+
 def kernel_source_hash():
-    """Hash of the device code the Dslash kernel is compiled from (kernel body, its helpers and types)."""
+    """Hash of the code the single-vector Dslash kernel is compiled from (kernel body, its helpers and
+    types), comments left out."""
     h = hashlib.sha256()
     for name in ("dslash_impl.cuh", "internal.cuh", "df64.cuh"):
-        with open(os.path.join(ROOT, "paper_2111_10354_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2111_10354_gb300", "csrc", name)) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -299,21 +308,31 @@ def antiherm_rel(torch, lat, prec):
     return abs(lhs - rhs) / abs(lhs)
 
 
-def time_dslash(torch, lat, prec, nrhs, reps, stream):
-    """Average device time of one Dslash launch (alternating D_oe, D_eo) with CUDA events on its stream."""
+def lanczos_record(st):
+    """A's extreme eigenvalues and condition number as a CG solve's Lanczos coefficients estimate them."""
+    if not st.get("lanczos_steps") or st["lambda_min"] <= 0:
+        return None
+    return {"lambda_min": float("%.5g" % st["lambda_min"]), "lambda_max": float("%.5g" % st["lambda_max"]),
+            "kappa": float("%.5g" % (st["lambda_max"] / st["lambda_min"])), "lanczos_steps": st["lanczos_steps"]}
+
+
+def time_dslash(torch, lat, prec, nrhs, reps, stream, interleaved=False):
+    """Average device time of one Dslash launch (alternating D_oe, D_eo) with CUDA events on its stream.
+    interleaved: the rhs-interleaved layout [cb][color][rhs] (the same Gaussian entries, placed per site)."""
     x = vec_like(torch, lat.half, prec, nrhs)
     y, z = torch.empty_like(x), torch.empty_like(x)
+    D = lat.dslash_interleaved if interleaved else lat.dslash
     torch.cuda.synchronize()  # x was written on torch's stream
     with torch.cuda.stream(stream):
         for _ in range(3):
-            lat.dslash(1, y, x, prec, nrhs)
-            lat.dslash(0, z, y, prec, nrhs)
+            D(1, y, x, prec, nrhs)
+            D(0, z, y, prec, nrhs)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(reps):
-            lat.dslash(1, y, x, prec, nrhs)
-            lat.dslash(0, z, y, prec, nrhs)
+            D(1, y, x, prec, nrhs)
+            D(0, z, y, prec, nrhs)
         e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / (2 * reps)
@@ -428,6 +447,9 @@ def run_ours(args, rank, world, local):
             rc, st = lat.cg(xs, b, m, TOL, 20000, **o)
             dt = time.perf_counter() - t0
             row[name] = {"s": round(dt, 4), "iters": st["iters"], "true_res": st["true_rel_residual"]}
+            if name == "fp64":
+                # the conditioning of this workload: Lanczos estimate from the FP64 solve's coefficients
+                row["lanczos_A"] = lanczos_record(st)
             if m == MASS:
                 sols[name] = xs.cpu().numpy()[0]
         cmp["m=%g" % m] = row
@@ -514,8 +536,8 @@ def run_sweep():
     for L in sizes:
         V = int(np.prod(L))
         # double-float links are resident too where they fit beside the others (not at 144^3x36, where
-        # FP64 + FP32 + FP16 already take 217 GB)
-        precs = (h.HISQ_F64, h.HISQ_F32, h.HISQ_F16) + ((h.HISQ_DF64,) if L[0] < 144 else ())
+        # FP64 + FP32 + FP16 + BF16 already take 248 GB)
+        precs = (h.HISQ_F64, h.HISQ_F32, h.HISQ_F16, h.HISQ_BF16) + ((h.HISQ_DF64,) if L[0] < 144 else ())
         lat = h.Lattice(L, precs=precs, stream=stream)
         # slab by slab keeps the host link arrays small even at 144^3x36
         nt = max(1, min(L[3], int(2e8 // (L[0] * L[1] * L[2] * 4 * 9 * 16))))
@@ -675,8 +697,10 @@ def row_batch(h, torch, hin):
                           "max_true_res": max(st["lattice_residual"]), "converged": st["converged"],
                           "kernel_launches": st["kernel_launches"],
                           "dslash_GBps_whole_solve": round(st["dslash_bytes"] / dt / 1e9, 1)}), flush=True)
-    # reference point: the same 64 solves one lattice at a time through hisq_cg
+    # reference point: the same 64 solves one lattice at a time through hisq_cg; an FP64 solve of each
+    # lattice (untimed) records its conditioning (Lanczos estimate from the CG coefficients)
     t = 0.0
+    kappas = []
     for l, m in enumerate(mix):
         lat = h.Lattice(m["dims"], precs=(h.HISQ_F64, h.HISQ_F32)).load(*lats[l])
         bl = torch.from_numpy(bs[l]).reshape(1, -1, 3).cuda()
@@ -685,8 +709,17 @@ def row_batch(h, torch, hin):
         xl.zero_()
         dt, _ = _timed(torch, lambda: lat.cg(xl, bl, m["mass"], 1e-10, 10000, inner_prec=h.HISQ_F32))
         t += dt
+        xl.zero_()
+        _, (_, st64) = _timed(torch, lambda: lat.cg(xl, bl, m["mass"], 1e-10, 10000, inner_prec=h.HISQ_F64))
+        rec = lanczos_record(st64)
+        if rec:
+            kappas.append((rec["kappa"], m["mass"], rec["lambda_min"], rec["lambda_max"]))
         lat.close()
-    print(json.dumps({"row": "batch", "variant": "64 sequential single-lattice mixed CG", "s": round(t, 4)}),
+    ks = sorted(k[0] for k in kappas)
+    print(json.dumps({"row": "batch", "variant": "64 sequential single-lattice mixed CG", "s": round(t, 4),
+                      "kappa_A": {"min": ks[0], "median": ks[len(ks) // 2], "max": ks[-1],
+                                  "lambda_min_over_4m2": [float("%.4g" % (k[2] / (4 * k[1] ** 2)))
+                                                          for k in sorted(kappas)[::16]]} if ks else None}),
           flush=True)
 
 
@@ -756,7 +789,8 @@ def row_learned(h, torch, hin, epochs=6, batch_pairs=16):
                           "mixed_cg": {"s": round(dt_c, 4), "iters": st_c["iters"],
                                        "true_res": st_c["true_rel_residual"]},
                           "fp64_cg": {"s": round(dt_d, 4), "iters": st_d["iters"],
-                                      "true_res": st_d["true_rel_residual"]}}), flush=True)
+                                      "true_res": st_d["true_rel_residual"]},
+                          "lanczos_A": lanczos_record(st_d)}), flush=True)
 
 
 SMEAR_LEVEL1 = dict(c1=1 / 8, c3=1 / 16, c5=1 / 64, c7=1 / 384)  # fat7

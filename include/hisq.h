@@ -4,10 +4,9 @@
  * The library applies the even/odd halves D_eo / D_oe of the HISQ staggered Dirac
  * operator and solves with A = M^dag M = 4 m^2 - D_eo D_oe by CG (plain FP64, mixed
  * precision with FP64 reliable updates, several right-hand sides) and multi-shift CG.
- * These are the operations the paper singles out: "applying the Dslash operator to a
- * vector" is "the most performance-critical kernel" of the CG that takes about 60% of
- * HISQ RHMC time, and the CG comes in multi-RHS, multi-shift and mixed-precision forms
- * (Sec. 3 and the module list of Sec. 2).
+ * These are the operations the paper singles out: the Dslash stencil dominates the cost of
+ * the CG, the CG takes about 60% of HISQ RHMC time, and the CG comes in multi-RHS,
+ * multi-shift and mixed-precision forms (Sec. 3 and the module list of Sec. 2).
  *
  * Conventions (the paper writes no formula; these are the textbook HISQ ones):
  *   lattice    dims = {Lx, Ly, Lz, Lt}, each even and >= 4; periodic index wrap.
@@ -89,7 +88,8 @@ typedef enum { HISQ_F64 = 0, HISQ_F32 = 1, HISQ_F16 = 2, HISQ_BF16 = 3, HISQ_DF6
 typedef struct hisq_ctx hisq_ctx;
 
 /*
- * Create a context for one lattice. dims: {Lx, Ly, Lz, Lt}, each even and >= 4.
+ * Create a context for one lattice (the gauge-field container of Sec. 2: one lattice, its links
+ * and fields held in device memory). dims: {Lx, Ly, Lz, Lt}, each even and >= 4.
  * prec_mask: OR of HISQ_PREC_BIT(p) for every storage precision whose links should
  * be kept resident (HISQ_F64 is always added: reliable updates and true residuals
  * need it). stream: a cudaStream_t (NULL = legacy default stream), borrowed.
@@ -102,8 +102,9 @@ int hisq_create(hisq_ctx** out, const int dims[4], unsigned prec_mask, void* str
 int hisq_destroy(hisq_ctx* ctx);
 
 /*
- * Load fat and long links for the whole lattice (host or device arrays in the link
- * layout above, V*4*9 complex128 each). flags: HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T.
+ * Load fat and long links for the whole lattice (the link storage of Sec. 2 and Sec. 3: the HISQ
+ * operator's smeared one-hop and Naik three-hop links, held in the precision each Dslash reads;
+ * host or device arrays in the link layout above, V*4*9 complex128 each). flags: HISQ_APPLY_PHASES | HISQ_ANTIPERIODIC_T.
  * The links are folded (phases, boundary sign) and converted to every resident
  * precision on the device; the input arrays are not kept. Returns HISQ_ENONFINITE if
  * any entry is NaN or Inf (the previous links are then no longer valid).
@@ -132,6 +133,8 @@ int hisq_load_links_slab(hisq_ctx* ctx, int t_begin, int t_count, const double* 
 int hisq_set_long_compression(hisq_ctx* ctx, double naik);
 
 /*
+ * The Dslash stencil whose cost dominates the CG and which is bound by memory bandwidth (Sec. 3);
+ * with nrhs > 1 one read of the links serves every vector, the multi-RHS form of Sec. 3.
  * out = D_eo in (out_parity = 0: out on even sites, in on odd sites), or
  * out = D_oe in (out_parity = 1). Vectors in precision prec (its links must be
  * resident), nrhs vectors of V/2 sites back to back; out and in must not overlap.
@@ -147,10 +150,27 @@ int hisq_set_long_compression(hisq_ctx* ctx, double naik);
 int hisq_dslash(hisq_ctx* ctx, int out_parity, void* out, const void* in, int prec, int nrhs);
 
 /*
- * out = (4 m^2 + sigma) in - D_eo D_oe in on even sites (the operator CG inverts,
- * shifted by sigma). Same vector conventions as hisq_dslash.
+ * out = (4 m^2 + sigma) in - D_eo D_oe in on even sites: the even-site operator M^dag M that the
+ * CG of Sec. 2 and Sec. 3 inverts (two Dslash applications per CG iteration), shifted by sigma as
+ * the multi-shift CG needs it. Same vector conventions as hisq_dslash. Errors as hisq_dslash, and
+ * HISQ_EINVAL for mass < 0 or sigma < 0.
  */
 int hisq_apply_A(hisq_ctx* ctx, void* out, const void* in, double mass, double sigma, int prec, int nrhs);
+
+/*
+ * The same two operators on the rhs-interleaved vector layout [cb][color][rhs]: the nrhs vectors of
+ * one site are one contiguous block of 3 rows (colours) of nrhs complex numbers (out, in: V/2 such
+ * blocks). This is the multi-RHS form of Sec. 3 laid out for the stencil: each of the 16 hops reads a
+ * neighbour's vectors as one block with 16-byte loads, and one launch applies every link to all nrhs
+ * vectors.
+ * nrhs: 1..64, a multiple of 2 for HISQ_F32 and of 4 for HISQ_F16 / HISQ_BF16 (any for HISQ_F64 and
+ * HISQ_DF64). Arithmetic, staging of host vectors and errors as hisq_dslash / hisq_apply_A
+ * (HISQ_EINVAL also for an nrhs that is not such a multiple). The launch form (vectors per thread)
+ * and block size are chosen by the autotuner at the first call per (precision, nrhs).
+ */
+int hisq_dslash_interleaved(hisq_ctx* ctx, int out_parity, void* out, const void* in, int prec, int nrhs);
+int hisq_apply_A_interleaved(hisq_ctx* ctx, void* out, const void* in, double mass, double sigma, int prec,
+                             int nrhs);
 
 /* ---------------------------------------------------------------- solvers */
 typedef struct {
@@ -164,6 +184,11 @@ typedef struct {
   int poll_every;       /* iterations between host convergence polls (default 25) */
   int reliable_prec;    /* operator precision of reliable updates and true residuals:
                            HISQ_F64 (default) or HISQ_DF64 (its links must be resident) */
+  int vector_layout;    /* inner vectors of a mixed-precision solve with an even number of rhs:
+                           0 (default) [rhs][cb][color], 1 interleaved per site ([cb][color][rhs],
+                           read by the interleaved multi-RHS Dslash). Results agree up to rounding
+                           order; the caller's x and b keep the boundary layout either way. On
+                           GB300 the default is the faster at every rhs count measured */
 } hisq_solver_opts;
 
 typedef struct {
@@ -177,12 +202,30 @@ typedef struct {
   int shift_iters[64];        /* multi-shift: iteration at which each shift converged */
   double shift_residual[64];  /* true residual of each shift (multi-shift) or rhs (CG) */
   long long kernel_launches;  /* CUDA kernels this call executed (graph nodes included) */
+  /* hisq_cg: estimates of the extreme eigenvalues of the solved operator (A + sigma of rhs 0) from
+     the Lanczos tridiagonal matrix of rhs 0's CG coefficients (hisq_lanczos_extremes), over its
+     longest run of iterations without a restart of the search direction; their ratio estimates the
+     condition number. lanczos_steps = coefficients recorded (restart marks included). 0 if none. */
+  double lambda_min, lambda_max;
+  int lanczos_steps;
 } hisq_solver_stats;
+
+/*
+ * Extreme eigenvalues of the Lanczos tridiagonal matrix that n CG coefficients define (alpha_k, beta_k
+ * of iteration k: x += alpha_k p, p = r + beta_k p): T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1},
+ * T_k,k+1 = sqrt(beta_k)/alpha_k, over the longest run of entries with alpha > 0 (alpha = 0 marks a
+ * restart). They bound A's extreme eigenvalues from inside and converge to them as CG converges
+ * (the Lanczos connection of CG, textbook; the paper has none). Host only; bisection on Sturm counts
+ * to ~1e-15 relative. Errors: HISQ_EINVAL (null pointer, n < 1, no positive alpha).
+ */
+int hisq_lanczos_extremes(const double* alpha, const double* beta, int n, double* lmin, double* lmax);
 
 /* Fill opts with the defaults above (inner_prec = HISQ_F64). */
 void hisq_solver_opts_default(hisq_solver_opts* opts);
 
 /*
+ * The CG of Sec. 2 (module list: CG with multi-RHS and mixed-precision variants) and Sec. 3 (the
+ * CG that takes about 60% of RHMC time), on the even-site operator A.
  * Solve A x_r = b_r (A = 4 m^2 - D_eo D_oe) for nrhs right-hand sides at once, each to
  * ||b_r - A x_r|| <= rel_tol ||b_r||, judged by the true FP64 residual at exit.
  * x: complex128 [nrhs][V/2][3], the initial guess on entry (zero is fine) and the
@@ -302,7 +345,8 @@ int hisq_fcg(hisq_ctx* ctx, hisq_ptc* ptc, double* x, const double* b, double ma
  * in, out: device pointers only (host vectors would need staging buffers); nrhs * V/2 * 6 *
  * sizeof(real of prec) must not exceed HISQ_NOALLOC_SCRATCH_BYTES, else HISQ_EINVAL.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, once per
- * device, with that device current); make that first call before any stream capture.
+ * device, with that device current); make that first call before any stream capture. The device
+ * current at the call must be the one that was current at hisq_create, else HISQ_EINVAL.
  * All calls share the array: calls whose work overlaps on the GPU (several streams or host
  * threads at once) race on it. Nothing in it needs clearing: each call overwrites what it reads.
  */

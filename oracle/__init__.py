@@ -6,8 +6,8 @@ CG and multi-shift CG. Only tests/, the package smoke check and the CPU-baseline
 bench.py may import this module. The CUDA library shares no code with it.
 
 Each function cites the passage it follows:
-  * Dslash: the operator the paper's performance section benchmarks ("applying the Dslash
-    operator to a vector is the most performance-critical kernel", Sec. 3); HISQ action
+  * Dslash: the operator the paper's performance section benchmarks, the stencil that
+    dominates the CG's cost (Sec. 3); HISQ action
     (Sec. 1, Sec. 2). The paper writes no formula, so the textbook staggered operator with
     fat one-hop and Naik three-hop long links is used (the readings are listed in oracle.c).
   * CG, multi-shift CG, multi-RHS: Sec. 2 (list of modules) and Sec. 3 (CG in RHMC).

@@ -9,8 +9,8 @@
  *
  * What the method computes (the paper names the operator, the CG variants and
  * RHMC but writes none of them out, so the textbook definitions are used):
- *   - the HISQ Dslash, "the most performance-critical kernel" of the CG that
- *     takes about 60% of RHMC time (Sec. 3);
+ *   - the HISQ Dslash, the stencil whose cost dominates the CG that in turn takes
+ *     about 60% of RHMC time (Sec. 3);
  *   - CG on M^dag M with multi-RHS, multi-shift and mixed-precision variants (Sec. 2,
  *     list of modules; Sec. 3);
  *   - HISQ fermions in RHMC (Sec. 1, Sec. 2).

@@ -41,7 +41,7 @@ def HISQ_PREC_BIT(p: int) -> int:
 
 class hisq_solver_opts(ctypes.Structure):
     _fields_ = [("inner_prec", ctypes.c_int), ("reliable_period", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("poll_every", ctypes.c_int), ("reliable_prec", ctypes.c_int)]
+                ("poll_every", ctypes.c_int), ("reliable_prec", ctypes.c_int), ("vector_layout", ctypes.c_int)]
 
 
 class hisq_solver_stats(ctypes.Structure):
@@ -49,7 +49,8 @@ class hisq_solver_stats(ctypes.Structure):
                 ("true_rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("dslash_bytes", ctypes.c_double), ("dslash_calls", ctypes.c_longlong),
                 ("shift_iters", ctypes.c_int * 64), ("shift_residual", ctypes.c_double * 64),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("lambda_min", ctypes.c_double),
+                ("lambda_max", ctypes.c_double), ("lanczos_steps", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("shift_iters", "shift_residual")}
@@ -91,6 +92,10 @@ def _load():
     lib.hisq_dslash.argtypes = [vp, ip, vp, vp, ip, ip]
     lib.hisq_apply_A.argtypes = [vp, vp, vp, dp, dp, ip, ip]
     lib.hisq_apply_A_noalloc.argtypes = [vp, vp, vp, dp, dp, ip, ip]
+    lib.hisq_dslash_interleaved.argtypes = [vp, ip, vp, vp, ip, ip]
+    lib.hisq_lanczos_extremes.argtypes = [vp, vp, ip, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+    lib.hisq_apply_A_interleaved.argtypes = [vp, vp, vp, dp, dp, ip, ip]
     lib.hisq_solver_opts_default.argtypes = [ctypes.POINTER(hisq_solver_opts)]
     lib.hisq_solver_opts_default.restype = None
     lib.hisq_cg.argtypes = [vp, vp, vp, ip, dp, dp, ip, ctypes.POINTER(hisq_solver_opts),
@@ -227,6 +232,30 @@ def hisq_apply_A(ctx, out, in_, mass: float, sigma: float, prec: int, nrhs: int 
     _check(_load().hisq_apply_A(ctx, _ptr(out), _ptr(in_), mass, sigma, prec, nrhs), "hisq_apply_A")
 
 
+def hisq_dslash_interleaved(ctx, out_parity: int, out, in_, prec: int, nrhs: int):
+    """hisq_dslash on the rhs-interleaved layout [cb][color][rhs]."""
+    _check(_load().hisq_dslash_interleaved(ctx, out_parity, _ptr(out), _ptr(in_), prec, nrhs),
+           "hisq_dslash_interleaved")
+
+
+def hisq_apply_A_interleaved(ctx, out, in_, mass: float, sigma: float, prec: int, nrhs: int):
+    """hisq_apply_A on the rhs-interleaved layout [cb][color][rhs]."""
+    _check(_load().hisq_apply_A_interleaved(ctx, _ptr(out), _ptr(in_), mass, sigma, prec, nrhs),
+           "hisq_apply_A_interleaved")
+
+
+def hisq_lanczos_extremes(alpha, beta):
+    """Extreme eigenvalues of the Lanczos tridiagonal matrix of CG coefficients alpha, beta (host)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    if a.shape != b.shape:
+        raise ValueError("alpha and beta differ in length")
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(_load().hisq_lanczos_extremes(a.ctypes.data, b.ctypes.data, len(a), ctypes.byref(lo), ctypes.byref(hi)),
+           "hisq_lanczos_extremes")
+    return lo.value, hi.value
+
+
 def hisq_apply_A_noalloc(ctx, out, in_, mass: float, sigma: float, prec: int, nrhs: int = 1):
     """hisq_apply_A without any device allocation (fixed scratch array; device vectors only)."""
     _check(_load().hisq_apply_A_noalloc(ctx, _ptr(out), _ptr(in_), mass, sigma, prec, nrhs), "hisq_apply_A_noalloc")
@@ -239,11 +268,12 @@ def hisq_solver_opts_default() -> hisq_solver_opts:
 
 
 def make_opts(inner_prec: int = HISQ_F64, reliable_period: int = 50, use_graph: bool = True, poll_every: int = 25,
-              reliable_prec: int = HISQ_F64):
+              reliable_prec: int = HISQ_F64, vector_layout: int = 0):
     o = hisq_solver_opts_default()
     o.inner_prec, o.reliable_period, o.use_graph, o.poll_every = inner_prec, reliable_period, int(use_graph), \
         poll_every
     o.reliable_prec = reliable_prec
+    o.vector_layout = vector_layout
     return o
 
 
@@ -563,6 +593,12 @@ class Lattice:
 
     def apply_A(self, out, in_, mass, prec, nrhs=1, sigma=0.0):
         hisq_apply_A(self.ctx, out, in_, mass, sigma, prec, nrhs)
+
+    def dslash_interleaved(self, out_parity, out, in_, prec, nrhs):
+        hisq_dslash_interleaved(self.ctx, out_parity, out, in_, prec, nrhs)
+
+    def apply_A_interleaved(self, out, in_, mass, prec, nrhs, sigma=0.0):
+        hisq_apply_A_interleaved(self.ctx, out, in_, mass, sigma, prec, nrhs)
 
     def cg(self, x, b, mass, rel_tol=1e-10, maxiter=10000, nrhs=1, **opts):
         return hisq_cg(self.ctx, x, b, nrhs, mass, rel_tol, maxiter, make_opts(**opts))

@@ -17,6 +17,11 @@ int dslash_launch_f16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_bf16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_df64(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_mma_launch(hisq_ctx* ctx, int prec, const DslashCall& c);
+int mrhs_launch_f64(hisq_ctx* ctx, int sp, const DslashCall& c);
+int mrhs_launch_f32(hisq_ctx* ctx, int sp, const DslashCall& c);
+int mrhs_launch_f16(hisq_ctx* ctx, int sp, const DslashCall& c);
+int mrhs_launch_bf16(hisq_ctx* ctx, int sp, const DslashCall& c);
+int mrhs_launch_df64(hisq_ctx* ctx, int sp, const DslashCall& c);
 
 static thread_local char g_last_error[512] = "";
 
@@ -112,8 +117,20 @@ static int dslash_launch_16bit_multi(hisq_ctx* ctx, int lp, const DslashCall& c)
   return HISQ_OK;
 }
 
+static int mrhs_launch_core(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
+  switch (lp) {
+    case HISQ_F64: return mrhs_launch_f64(ctx, sp, c);
+    case HISQ_F32: return mrhs_launch_f32(ctx, sp, c);
+    case HISQ_F16: return mrhs_launch_f16(ctx, sp, c);
+    case HISQ_BF16: return mrhs_launch_bf16(ctx, sp, c);
+    case HISQ_DF64: return mrhs_launch_df64(ctx, sp, c);
+  }
+  return set_error(HISQ_EINVAL, "bad precision %d", lp);
+}
+
 int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
   if (!ctx->links[lp]) return set_error(HISQ_EINVAL, "link precision %d is not resident", lp);
+  if (c.interleaved) return mrhs_launch_core(ctx, lp, sp, c);
   const bool compressed = ctx->naik != 0.0 && ctx->long12[lp] != nullptr;
   if ((lp == HISQ_F16 || lp == HISQ_BF16) && sp == lp && c.epi == EPI_PLAIN && c.nrhs >= 8 && !compressed)
     return dslash_launch_16bit_multi(ctx, lp, c);
@@ -287,6 +304,7 @@ int hisq_create(hisq_ctx** out, const int dims[4], unsigned prec_mask, void* str
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  c->device = dev;
   if (e != cudaSuccess) {
     delete c;
     return cuda_error(e, "device query");
@@ -425,7 +443,8 @@ static int stage_in(hisq_ctx* c, const void* p, size_t bytes, const char* name, 
   return HISQ_OK;
 }
 
-int hisq_dslash(hisq_ctx* c, int out_parity, void* out, const void* in, int prec, int nrhs) {
+static int dslash_entry(hisq_ctx* c, int out_parity, void* out, const void* in, int prec, int nrhs,
+                        bool interleaved) {
   int rc = check_vec_args(c, prec, nrhs);
   if (rc != HISQ_OK) return rc;
   if (out_parity != 0 && out_parity != 1) return set_error(HISQ_EINVAL, "parity %d", out_parity);
@@ -443,6 +462,7 @@ int hisq_dslash(hisq_ctx* c, int out_parity, void* out, const void* in, int prec
   call.in = d_in;
   call.nrhs = nrhs;
   call.rhs_stride = c->g.half;
+  call.interleaved = interleaved;
   rc = dslash_launch(c, prec, prec, call);
   if (rc != HISQ_OK) return rc;
   if (host_out) {
@@ -452,7 +472,8 @@ int hisq_dslash(hisq_ctx* c, int out_parity, void* out, const void* in, int prec
   return HISQ_OK;
 }
 
-int hisq_apply_A(hisq_ctx* c, void* out, const void* in, double mass, double sigma, int prec, int nrhs) {
+static int apply_A_entry(hisq_ctx* c, void* out, const void* in, double mass, double sigma, int prec, int nrhs,
+                         bool interleaved) {
   int rc = check_vec_args(c, prec, nrhs);
   if (rc != HISQ_OK) return rc;
   if (!out || !in || out == in) return set_error(HISQ_EINVAL, "null or aliased vectors");
@@ -471,6 +492,7 @@ int hisq_apply_A(hisq_ctx* c, void* out, const void* in, double mass, double sig
   c1.in = d_in;
   c1.nrhs = nrhs;
   c1.rhs_stride = c->g.half;
+  c1.interleaved = interleaved;
   if ((rc = dslash_launch(c, prec, prec, c1)) != HISQ_OK) return rc;
   DslashCall c2 = c1;
   c2.out_parity = 0;
@@ -485,6 +507,23 @@ int hisq_apply_A(hisq_ctx* c, void* out, const void* in, double mass, double sig
     HISQ_CUDA(cudaStreamSynchronize(c->stream));
   }
   return HISQ_OK;
+}
+
+int hisq_dslash(hisq_ctx* c, int out_parity, void* out, const void* in, int prec, int nrhs) {
+  return dslash_entry(c, out_parity, out, in, prec, nrhs, false);
+}
+
+int hisq_dslash_interleaved(hisq_ctx* c, int out_parity, void* out, const void* in, int prec, int nrhs) {
+  return dslash_entry(c, out_parity, out, in, prec, nrhs, true);
+}
+
+int hisq_apply_A(hisq_ctx* c, void* out, const void* in, double mass, double sigma, int prec, int nrhs) {
+  return apply_A_entry(c, out, in, mass, sigma, prec, nrhs, false);
+}
+
+int hisq_apply_A_interleaved(hisq_ctx* c, void* out, const void* in, double mass, double sigma, int prec,
+                             int nrhs) {
+  return apply_A_entry(c, out, in, mass, sigma, prec, nrhs, true);
 }
 
 long long hisq_launch_count(const hisq_ctx* c) { return c ? c->launches : 0; }

@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <cmath>
 #include <type_traits>
 #include <vector>
 
@@ -95,6 +96,27 @@ __global__ void k_residual_zero(const double2* __restrict__ b, size_t b_stride, 
     }
 }
 
+// Bookkeeping of a reliable update (one thread): per-rhs verification, rescaling and the new cycle.
+__device__ __forceinline__ void reliable_commit(SolverState* st, size_t n) {
+  // the search direction restarts: the Lanczos relation of rhs 0's coefficients ends here
+  if (st->lanczos && st->lanczos_n > 0 && st->lanczos_n < st->lanczos_cap && st->lanczos[st->lanczos_n - 1] != 0.0)
+    st->lanczos[st->lanczos_n++] = 0.0;
+  bool all = true;
+  for (int q = 0; q < st->nrhs; ++q) {
+    const bool c = st->rr_true[q] <= st->tol2[q];
+    st->rhs_conv[q] = c;
+    st->rhs_done[q] = c;
+    const double s = sqrt(st->rr_true[q] / (double)n);
+    if (!c && s > 0.0) {
+      st->scale[q] = s;
+      st->rr[q] = st->rr_true[q] / (s * s);
+    }
+    all = all && c;
+  }
+  st->done = all ? 1 : 0;
+  st->cycle_iter = 0;
+}
+
 // Reliable update: for each rhs not yet verified, r_lo = r_hi / s (s = RMS entry of r_hi),
 // p = r_lo (restart); rr = |r_hi|^2 / s^2. Verified rhs are frozen.
 template <typename S>
@@ -116,22 +138,7 @@ __global__ void k_reliable(const double2* __restrict__ r_hi, S* __restrict__ r_l
       p[2 * (off + i) + 1] = im;
     }
   }
-  if (last_block_done(counter) && threadIdx.x == 0) {
-    bool all = true;
-    for (int q = 0; q < st->nrhs; ++q) {
-      const bool c = st->rr_true[q] <= st->tol2[q];
-      st->rhs_conv[q] = c;
-      st->rhs_done[q] = c;
-      const double s = sqrt(st->rr_true[q] / (double)n);
-      if (!c && s > 0.0) {
-        st->scale[q] = s;
-        st->rr[q] = st->rr_true[q] / (s * s);
-      }
-      all = all && c;
-    }
-    st->done = all ? 1 : 0;
-    st->cycle_iter = 0;
-  }
+  if (last_block_done(counter) && threadIdx.x == 0) reliable_commit(st, n);
 }
 
 
@@ -302,6 +309,363 @@ __global__ void k_new_cycle(SolverState* st) {
   st->cycle_iter = 0;
 }
 
+// ------------------------------------------------------------------ fused update (one launch per iteration)
+// Commit of one iteration by the last block at the fused update's grid barrier (one thread): tot[q] =
+// |r_q|^2 after the r update. Forms beta = rr_new / rr, commits rr, per-rhs inner convergence, the
+// iteration counts and the end-of-cycle flag (the bookkeeping of k_update's and k_pupdate's last blocks).
+__device__ __forceinline__ void commit_iteration(SolverState* st, const double* tot) {
+  if (st->lanczos && !st->rhs_done[0] && st->lanczos_n < st->lanczos_cap) {
+    st->lanczos[st->lanczos_n] = st->rr[0] / st->pAp[0];                      // alpha
+    st->lanczos[st->lanczos_cap + st->lanczos_n] = tot[0] / st->rr[0];      // beta
+    st->lanczos_n += 1;
+  }
+  bool all = true;
+  for (int q = 0; q < st->nrhs; ++q) {
+    st->rr_new[q] = tot[q];
+    if (!st->rhs_done[q]) {
+      if (!(st->pAp[q] > 0.0)) st->breakdown = 1;
+      if (!isfinite(tot[q])) st->nonfinite = 1;
+      st->beta[q] = tot[q] / st->rr[q];
+      st->rr[q] = tot[q];
+      const double s = st->scale[q];
+      if (st->rr[q] * s * s <= st->tol2[q]) st->rhs_done[q] = 1;
+    }
+    all = all && st->rhs_done[q];
+  }
+  st->iter += 1;
+  st->cycle_iter += 1;
+  if (all || st->cycle_iter >= st->cycle_limit || st->breakdown || st->nonfinite) st->done = 1;
+}
+
+// The last block's part of the barrier: each warp sums the partials of some rhs ([rhs][gridDim.x x
+// gridDim.y blocks], fixed order per lane, then a fixed shuffle tree), thread 0 commits the iteration.
+__device__ __forceinline__ void finish_iteration(SolverState* st, const double* partials, int nblk, double* s_tot) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
+  const int nrhs = st->nrhs;
+  // whole warps only (a block of P * S threads may end in a partial warp)
+  for (int q = warp; warp < nw && q < nrhs; q += nw) {
+    double t = 0.0;
+    for (int b = lane; b < nblk; b += 32) t += __ldcg(partials + (size_t)q * nblk + b);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) s_tot[q] = t;
+  }
+  __syncthreads();
+  if (tid == 0) commit_iteration(st, s_tot);
+}
+
+// One CG iteration's vector updates in one launch on the blocked layout [rhs][cb][color] (grid: x
+// chunks of a rhs, y = rhs; a cooperative launch of one wave):
+//   phase 1: r -= alpha Ap (alpha = rr / pAp), rr_new = |r|^2 (per-chunk terms in the arithmetic
+//            precision, FP64 over chunks);
+//   barrier: the last block to arrive forms rr_new and beta per rhs and commits the iteration;
+//   phase 2: x += alpha p (X = double: the FP64 solution, X = float: the cycle's FP32 correction);
+//            p = r + beta p.
+// The first KEEP chunks of r a thread updates stay in registers for phase 2; further chunks are read
+// again. Each thread handles its chunks in batches of KEEP whose loads are all issued before any store. Vector traffic: Ap, r read and r written, then p, x (and r beyond KEEP) read and p, x written:
+// seven vector passes where the two-launch form (k_update + k_pupdate) takes nine.
+template <typename S, typename X, int KEEP>
+__global__ void __launch_bounds__(256, 2) k_cg_update(X* __restrict__ x, S* __restrict__ r, S* __restrict__ p,
+                                                   const S* __restrict__ Ap, size_t n, SolverState* st,
+                                                   double* partials, unsigned* bar) {
+  using T = typename Real<S>::acc;
+  using XT = typename Real<X>::acc;
+  constexpr int K = Chunk<S>::K;
+  __shared__ double red[32];
+  __shared__ double s_tot[MAXR];
+  if (st->done) return;  // uniform: only the last block at the barrier changes it
+  const int rh = blockIdx.y;
+  const size_t off = (size_t)rh * n;
+  const double pap = st->pAp[rh];
+  const bool frozen = st->rhs_done[rh] != 0;
+  const bool active = !frozen && pap > 0.0 && isfinite(pap);
+  const double alpha = active ? st->rr[rh] / pap : 0.0;
+  const T a = T(alpha);
+  const XT ax = XT(sizeof(X) == 8 ? alpha * st->scale[rh] : alpha);
+  const size_t stride = (size_t)gridDim.x * blockDim.x * K;
+  const size_t i0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K;
+  const size_t nn = frozen ? 0 : n;  // a frozen rhs's vectors are not touched
+  cplx<T> keep[KEEP][K];
+  double v = 0.0;
+  // phase 1 in batches of KEEP chunks: every load of a batch is issued before any store (r is read and
+  // written, so a store would otherwise keep the next chunk's loads from being issued early)
+  auto phase1 = [&](size_t ib, cplx<T>(&rv)[KEEP][K]) {
+    cplx<T> av[KEEP][K];
+#pragma unroll
+    for (int j = 0; j < KEEP; ++j) {
+      const size_t i = ib + j * stride;
+      if (i < nn) {
+        Chunk<S>::load(r, (off + i) / K, rv[j]);
+        if (active) Chunk<S>::load(Ap, (off + i) / K, av[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < KEEP; ++j) {
+      const size_t i = ib + j * stride;
+      if (i < nn) {
+        T t = T(0);
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          if (active) {
+            rv[j][c].re = fma(-a, av[j][c].re, rv[j][c].re);
+            rv[j][c].im = fma(-a, av[j][c].im, rv[j][c].im);
+          }
+          t += rv[j][c].re * rv[j][c].re + rv[j][c].im * rv[j][c].im;
+        }
+        if (active) Chunk<S>::store(r, (off + i) / K, rv[j]);
+        v += (double)t;
+      }
+    }
+  };
+  phase1(i0, keep);  // the first batch stays in registers for phase 2
+  for (size_t ib = i0 + KEEP * stride; ib < nn; ib += KEEP * stride) {
+    cplx<T> rv[KEEP][K];
+    phase1(ib, rv);
+  }
+  const double bs = block_sum_dyn(v, red);
+  if (threadIdx.x == 0) partials[(size_t)rh * gridDim.x + blockIdx.x] = bs;
+  unsigned gen;
+  if (grid_arrive(bar, &gen)) {
+    finish_iteration(st, partials, gridDim.x, s_tot);
+    grid_release(bar);
+  } else if (!grid_wait(bar, gen)) {
+    if (threadIdx.x == 0) {
+      st->timeout = 1;
+      st->done = 1;
+    }
+    return;
+  }
+  if (!active) return;
+  const T beta = T(__ldcg(&st->beta[rh]));
+  // phase 2, batch by batch: loads first, then x += alpha p, p = r + beta p, then stores
+  auto phase2 = [&](size_t ib, const cplx<T>(&rv)[KEEP][K]) {
+    cplx<T> pv[KEEP][K];
+    cplx<XT> xv[KEEP][K];
+#pragma unroll
+    for (int j = 0; j < KEEP; ++j) {
+      const size_t i = ib + j * stride;
+      if (i < nn) {
+        Chunk<S>::load(p, (off + i) / K, pv[j]);
+        load_k<X, K>(x, off + i, xv[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < KEEP; ++j) {
+      const size_t i = ib + j * stride;
+      if (i < nn) {
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          xv[j][c].re = fma(ax, XT(pv[j][c].re), xv[j][c].re);
+          xv[j][c].im = fma(ax, XT(pv[j][c].im), xv[j][c].im);
+          pv[j][c].re = fma(beta, pv[j][c].re, rv[j][c].re);
+          pv[j][c].im = fma(beta, pv[j][c].im, rv[j][c].im);
+        }
+        store_k<X, K>(x, off + i, xv[j]);
+        Chunk<S>::store(p, (off + i) / K, pv[j]);
+      }
+    }
+  };
+  phase2(i0, keep);
+  for (size_t ib = i0 + KEEP * stride; ib < nn; ib += KEEP * stride) {
+    cplx<T> rv[KEEP][K];
+#pragma unroll
+    for (int j = 0; j < KEEP; ++j) {
+      const size_t i = ib + j * stride;
+      if (i < nn) Chunk<S>::load(r, (off + i) / K, rv[j]);
+    }
+    phase2(ib, rv);
+  }
+}
+
+// ------------------------------------------------------------------ rhs-interleaved inner vectors
+// Mixed-precision multi-RHS solves with an even number N of rhs keep their FP32 inner vectors in the
+// rhs-interleaved layout [cb][color][rhs] that the interleaved Dslash reads. Every 16-byte word holds
+// one colour of rhs 2q and 2q+1 at one site: word w = (3 cb + colour) P + q with P = N / 2. A block of
+// P * S threads (S a power of two) and a grid stride that is a multiple of P keep q = tid % P fixed
+// for every word a thread touches, so each thread carries the scalars of one rhs pair.
+__device__ __forceinline__ void wload(const float* base, size_t w, cplx<float> (&v)[2]) {
+  const float4 a = reinterpret_cast<const float4*>(base)[w];
+  v[0] = {a.x, a.y};
+  v[1] = {a.z, a.w};
+}
+__device__ __forceinline__ void wstore(float* base, size_t w, const cplx<float> (&v)[2]) {
+  reinterpret_cast<float4*>(base)[w] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+}
+
+// Sum of v[0..1] over the S slots (tid / P) of the block for each rhs pair q = tid % P (a tree over S);
+// the threads tid < P get the totals of pair tid.
+__device__ __forceinline__ void il_block_sum(double (&v)[2], int P, double* red /* [2][blockDim] */) {
+  const int S = blockDim.x / P, q = threadIdx.x % P, y = threadIdx.x / P, nt = P * S;
+  red[y * P + q] = v[0];
+  red[nt + y * P + q] = v[1];
+  __syncthreads();
+  for (int h = S >> 1; h > 0; h >>= 1) {
+    if (y < h) {
+      red[y * P + q] += red[(y + h) * P + q];
+      red[nt + y * P + q] += red[nt + (y + h) * P + q];
+    }
+    __syncthreads();
+  }
+  v[0] = red[q];
+  v[1] = red[nt + q];
+}
+
+// The fused update (as k_cg_update) on interleaved FP32 vectors; e: the cycle's FP32 correction,
+// interleaved as well. nw: 16-byte words per vector set (3 * half * P). Phase 2 reads r again (the N
+// vectors of a thread's words do not fit in registers).
+__global__ void __launch_bounds__(256) k_cg_update_il(float* __restrict__ e, float* __restrict__ r,
+                                                      float* __restrict__ p, const float* __restrict__ Ap,
+                                                      size_t nw, int P, SolverState* st, double* partials,
+                                                      unsigned* bar) {
+  __shared__ double red[512];
+  __shared__ double s_tot[MAXR];
+  if (st->done) return;  // uniform: only the last block at the barrier changes it
+  const int q = threadIdx.x % P;
+  bool active[2], frozen[2];
+  float a[2];
+  for (int k = 0; k < 2; ++k) {
+    const int rh = 2 * q + k;
+    const double pap = st->pAp[rh];
+    frozen[k] = st->rhs_done[rh] != 0;
+    active[k] = !frozen[k] && pap > 0.0 && isfinite(pap);
+    a[k] = active[k] ? float(st->rr[rh] / pap) : 0.f;
+  }
+  const bool any = !frozen[0] || !frozen[1];
+  const size_t w0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  constexpr int BW = 4;  // words per batch: all loads of a batch are issued before its stores
+  double v[2] = {0.0, 0.0};
+  for (size_t wb = any ? w0 : nw; wb < nw; wb += BW * stride) {
+    cplx<float> rv[BW][2], av[BW][2];
+#pragma unroll
+    for (int j = 0; j < BW; ++j) {
+      const size_t w = wb + j * stride;
+      if (w < nw) {
+        wload(r, w, rv[j]);
+        if (active[0] || active[1]) wload(Ap, w, av[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BW; ++j) {
+      const size_t w = wb + j * stride;
+      if (w < nw) {
+        if (active[0] || active[1]) {
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            rv[j][k].re = fma(-a[k], av[j][k].re, rv[j][k].re);
+            rv[j][k].im = fma(-a[k], av[j][k].im, rv[j][k].im);
+          }
+          wstore(r, w, rv[j]);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) v[k] += (double)(rv[j][k].re * rv[j][k].re + rv[j][k].im * rv[j][k].im);
+      }
+    }
+  }
+  il_block_sum(v, P, red);
+  if (threadIdx.x < P) {
+    partials[(size_t)(2 * q) * gridDim.x + blockIdx.x] = v[0];
+    partials[(size_t)(2 * q + 1) * gridDim.x + blockIdx.x] = v[1];
+  }
+  unsigned gen;
+  if (grid_arrive(bar, &gen)) {
+    finish_iteration(st, partials, gridDim.x, s_tot);
+    grid_release(bar);
+  } else if (!grid_wait(bar, gen)) {
+    if (threadIdx.x == 0) {
+      st->timeout = 1;
+      st->done = 1;
+    }
+    return;
+  }
+  if (!active[0] && !active[1]) return;
+  float beta[2];
+  for (int k = 0; k < 2; ++k) beta[k] = active[k] ? float(__ldcg(&st->beta[2 * q + k])) : 0.f;
+  for (size_t wb = w0; wb < nw; wb += BW * stride) {
+    cplx<float> rv[BW][2], pv[BW][2], ev[BW][2];
+#pragma unroll
+    for (int j = 0; j < BW; ++j) {
+      const size_t w = wb + j * stride;
+      if (w < nw) {
+        wload(r, w, rv[j]);
+        wload(p, w, pv[j]);
+        wload(e, w, ev[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BW; ++j) {
+      const size_t w = wb + j * stride;
+      if (w >= nw) continue;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (!active[k]) continue;  // a frozen rhs keeps its p and e
+        ev[j][k].re = fma(a[k], pv[j][k].re, ev[j][k].re);
+        ev[j][k].im = fma(a[k], pv[j][k].im, ev[j][k].im);
+        pv[j][k].re = fma(beta[k], pv[j][k].re, rv[j][k].re);
+        pv[j][k].im = fma(beta[k], pv[j][k].im, rv[j][k].im);
+      }
+      wstore(e, w, ev[j]);
+      wstore(p, w, pv[j]);
+    }
+  }
+}
+
+// Reliable update on interleaved FP32 vectors: for each unverified rhs, r_lo = p = r_hi / s from the
+// blocked FP64 residual r_hi ([rhs][cb][color]); then (last block) the bookkeeping of k_reliable.
+__global__ void k_reliable_il(const double2* __restrict__ r_hi, float* __restrict__ r_lo, float* __restrict__ p,
+                              size_t nw, int P, SolverState* st, unsigned* counter) {
+  const int q = threadIdx.x % P;
+  const size_t n = nw / P;  // complex entries per rhs (3 * half)
+  double inv[2];
+  bool upd[2];
+  for (int k = 0; k < 2; ++k) {
+    const int rh = 2 * q + k;
+    const double s_new = sqrt(st->rr_true[rh] / (double)n);
+    upd[k] = !(st->rr_true[rh] <= st->tol2[rh]) && s_new > 0.0;
+    inv[k] = upd[k] ? 1.0 / s_new : 0.0;
+  }
+  if (upd[0] || upd[1]) {
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < nw; w += (size_t)gridDim.x * blockDim.x) {
+      const size_t entry = w / P;  // 3 cb + colour
+      cplx<float> rv[2], pv[2];
+      wload(r_lo, w, rv);
+      wload(p, w, pv);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (!upd[k]) continue;
+        const double2 h = r_hi[(size_t)(2 * q + k) * n + entry];
+        rv[k] = {float(h.x * inv[k]), float(h.y * inv[k])};
+        pv[k] = rv[k];
+      }
+      wstore(r_lo, w, rv);
+      wstore(p, w, pv);
+    }
+  }
+  if (last_block_done(counter) && threadIdx.x == 0) reliable_commit(st, n);
+}
+
+// End of a mixed-precision cycle on interleaved corrections: x (blocked FP64) += scale * e; e = 0.
+__global__ void k_fold_il(double2* __restrict__ x, float* __restrict__ e, size_t nw, int P, const SolverState* st) {
+  const int q = threadIdx.x % P;
+  const size_t n = nw / P;
+  const double s[2] = {st->scale[2 * q], st->scale[2 * q + 1]};
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < nw; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t entry = w / P;
+    cplx<float> ev[2];
+    wload(e, w, ev);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      double2* dst = x + (size_t)(2 * q + k) * n + entry;
+      double2 xv = *dst;
+      xv.x += s[k] * (double)ev[k].re;
+      xv.y += s[k] * (double)ev[k].im;
+      *dst = xv;
+    }
+    const cplx<float> z[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    wstore(e, w, z);
+  }
+}
+
 // ------------------------------------------------------------------ host driver
 struct CgBuffers {
   double2 *x, *b, *r_hi, *Ax, *t64;
@@ -313,7 +677,59 @@ struct CgBuffers {
   double* partials;
   int rp = HISQ_F64;     // operator precision of the true residual: HISQ_F64 or HISQ_DF64
   unsigned* rowc;        // per-rhs block counters of the row reductions [MAXR]
+  bool il = false;       // inner vectors (r, p, Ap, t, e) in the rhs-interleaved layout [cb][color][rhs]
+  int P = 0;             // il: rhs pairs per site (nrhs / 2)
+  int il_block = 0;      // il: threads per block of the interleaved BLAS kernels (P x a power of two)
+  dim3 upd_grid;         // the fused update's cooperative grid (one wave)
+  int upd_block = 256;
 };
+
+// Cooperative launch (every block resident at once: the fused update meets at a grid barrier).
+template <typename... Exp, typename... Act>
+static cudaError_t launch_cooperative(void (*kernel)(Exp...), dim3 grid, int block, cudaStream_t stream,
+                                      Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Act>(args)...);
+}
+
+// The fused update kernel for the buffers' layout and inner type.
+template <typename S>
+static const void* update_kernel(const CgBuffers& B) {
+  if (B.il) return (const void*)k_cg_update_il;
+  if constexpr (sizeof(S) == 8) return (const void*)k_cg_update<double, double, 4>;
+  return (const void*)k_cg_update<float, float, 4>;
+}
+
+// One wave of the fused update: as many blocks as are resident together, at most one per unit of work.
+template <typename S>
+static int plan_update(hisq_ctx* ctx, CgBuffers& B, int nrhs) {
+  int per_sm = 0;
+  B.upd_block = B.il ? B.il_block : 256;
+  HISQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, update_kernel<S>(B), B.upd_block, 0));
+  if (per_sm < 1) return set_error(HISQ_ECUDA, "fused CG update cannot be resident");
+  const size_t wave = (size_t)ctx->num_sms * per_sm;
+  if (B.il) {
+    const size_t words = (size_t)ctx->g.half * 3 * B.P;
+    size_t gx = (words + B.il_block - 1) / B.il_block;
+    B.upd_grid = dim3((unsigned)(gx < wave ? gx : wave), 1);
+  } else {
+    const size_t chunks = (size_t)ctx->g.half * 3 / Chunk<S>::K;
+    size_t gx = (chunks + B.upd_block - 1) / B.upd_block;
+    const size_t cap = wave / (size_t)nrhs;
+    if (cap < 1) return set_error(HISQ_EINVAL, "%d rhs exceed one wave of the fused CG update", nrhs);
+    B.upd_grid = dim3((unsigned)(gx < cap ? gx : cap), nrhs);
+  }
+  return HISQ_OK;
+}
 
 static dim3 blas_grid(const hisq_ctx* ctx, int nrhs, size_t units, int per_sm = 8) {
   size_t gx = (units + 255) / 256;
@@ -350,9 +766,25 @@ static int true_residual(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int init) 
   return HISQ_OK;
 }
 
+// Grid of the interleaved BLAS kernels: one thread per 16-byte word, at most one wave of 8 blocks per SM
+// (the grid stride stays a multiple of P, as every block is).
+static dim3 il_grid(const hisq_ctx* ctx, const CgBuffers& B) {
+  const size_t words = (size_t)ctx->g.half * 3 * B.P;
+  size_t gx = (words + B.il_block - 1) / B.il_block;
+  const size_t cap = (size_t)ctx->num_sms * 8;
+  return dim3((unsigned)(gx < cap ? gx : cap));
+}
+
 template <typename S>
 static int reliable(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int first) {
   const size_t n = (size_t)ctx->g.half * 3;
+  if (B.il) {
+    k_reliable_il<<<il_grid(ctx, B), B.il_block, 0, ctx->stream>>>(B.r_hi, (float*)B.r, (float*)B.p,
+                                                                   n * B.P, B.P, B.st, ctx->d_counters + 2);
+    HISQ_CUDA(cudaGetLastError());
+    note_launch(ctx);
+    return HISQ_OK;
+  }
   k_reliable<S><<<blas_grid(ctx, nrhs), 256, 0, ctx->stream>>>(B.r_hi, (S*)B.r, (S*)B.p, n, B.st, first,
                                                                ctx->d_counters + 2);
   HISQ_CUDA(cudaGetLastError());
@@ -373,6 +805,7 @@ static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
   c1.nrhs = nrhs;
   c1.rhs_stride = ctx->g.half;
   c1.skip = &B.st->done;
+  c1.interleaved = B.il;
   int rc = dslash_launch(ctx, lp, sp, c1);
   if (rc != HISQ_OK) return rc;
   DslashCall c2 = c1;
@@ -386,18 +819,76 @@ static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
   c2.dot_out = B.st->pAp;
   c2.counter = ctx->d_counters + 3;
   if ((rc = dslash_launch(ctx, lp, sp, c2)) != HISQ_OK) return rc;
-  // one thread per 16-byte chunk of each vector, one wave of resident blocks (6 or 8 per SM)
-  dim3 grid = blas_grid(ctx, nrhs, n / Chunk<S>::K, 6);
-  if constexpr (sizeof(S) == 8)
-    k_update<S, double><<<grid, 256, 0, ctx->stream>>>((double*)B.x, (S*)B.r, (const S*)B.p, (const S*)B.Ap, n,
-                                                       B.st, B.partials, partial_stride(ctx), B.rowc);
+  // the vector updates of the iteration: one cooperative launch meeting at a grid barrier
+  unsigned* bar = ctx->d_counters + 30;
+  cudaError_t e;
+  if (B.il)
+    e = launch_cooperative(k_cg_update_il, B.upd_grid, B.upd_block, ctx->stream, (float*)B.e, (float*)B.r,
+                           (float*)B.p, (const float*)B.Ap, n * B.P, B.P, B.st, B.partials, bar);
+  else if constexpr (sizeof(S) == 8)
+    e = launch_cooperative(k_cg_update<double, double, 4>, B.upd_grid, B.upd_block, ctx->stream, (double*)B.x,
+                           (double*)B.r, (double*)B.p, (const double*)B.Ap, n, B.st, B.partials, bar);
   else
-    k_update<S, float><<<grid, 256, 0, ctx->stream>>>((float*)B.e, (S*)B.r, (const S*)B.p, (const S*)B.Ap, n,
-                                                      B.st, B.partials, partial_stride(ctx), B.rowc);
-  k_pupdate<S><<<blas_grid(ctx, nrhs, n / Chunk<S>::K, 8), 256, 0, ctx->stream>>>((const S*)B.r, (S*)B.p, n, B.st,
-                                                                               ctx->d_counters + 5);
-  HISQ_CUDA(cudaGetLastError());
-  note_launch(ctx, 2);
+    e = launch_cooperative(k_cg_update<float, float, 4>, B.upd_grid, B.upd_block, ctx->stream, (float*)B.e,
+                           (float*)B.r, (float*)B.p, (const float*)B.Ap, n, B.st, B.partials, bar);
+  HISQ_CUDA(e);
+  note_launch(ctx);
+  return HISQ_OK;
+}
+
+// ------------------------------------------------------------------ Lanczos estimate of the spectrum
+// CG's coefficients define the Lanczos tridiagonal matrix T of A on the Krylov space of the source:
+// T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T_k,k+1 = sqrt(beta_k)/alpha_k. Its extreme eigenvalues
+// approach A's from inside as the iteration proceeds. They are found by bisection on the Sturm count
+// (the number of negative pivots of T - x I is the number of eigenvalues below x).
+static int sturm_count(const std::vector<double>& d, const std::vector<double>& e2, double x) {
+  int neg = 0;
+  double q = 1.0;
+  for (size_t k = 0; k < d.size(); ++k) {
+    q = d[k] - x - (k > 0 ? e2[k - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;  // a zero pivot counts as negative: x sits on an eigenvalue
+    if (q < 0.0) ++neg;
+  }
+  return neg;
+}
+
+int lanczos_extremes(const double* alpha, const double* beta, int n, double* lmin, double* lmax) {
+  // the longest run of coefficients between restarts (alpha = 0)
+  int best0 = 0, bestn = 0;
+  for (int k = 0; k < n;) {
+    int j = k;
+    while (j < n && alpha[j] > 0.0 && std::isfinite(alpha[j]) && beta[j] >= 0.0) ++j;
+    if (j - k > bestn) {
+      best0 = k;
+      bestn = j - k;
+    }
+    k = j + 1;
+  }
+  if (bestn < 1) return set_error(HISQ_EINVAL, "no Lanczos coefficients");
+  std::vector<double> d(bestn), e2(bestn > 1 ? bestn - 1 : 1, 0.0);
+  double lo = 1e300, hi = -1e300;
+  for (int k = 0; k < bestn; ++k) {
+    const double* a = alpha + best0;
+    const double* b = beta + best0;
+    d[k] = 1.0 / a[k] + (k > 0 ? b[k - 1] / a[k - 1] : 0.0);
+    if (k + 1 < bestn) e2[k] = b[k] / (a[k] * a[k]);
+  }
+  for (int k = 0; k < bestn; ++k) {  // Gershgorin bounds
+    const double r = (k > 0 ? sqrt(e2[k - 1]) : 0.0) + (k + 1 < bestn ? sqrt(e2[k]) : 0.0);
+    lo = fmin(lo, d[k] - r);
+    hi = fmax(hi, d[k] + r);
+  }
+  auto bisect = [&](int target) {  // the smallest x with count(x) > target
+    double a = lo, b = hi;
+    for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); ++it) {
+      const double m = 0.5 * (a + b);
+      if (sturm_count(d, e2, m) > target) b = m;
+      else a = m;
+    }
+    return 0.5 * (a + b);
+  };
+  *lmin = bisect(0);
+  *lmax = bisect(bestn - 1);
   return HISQ_OK;
 }
 
@@ -434,10 +925,27 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   SolverState* hst = (SolverState*)ctx->pinned;
   if (!B.r_hi || !B.Ax || !B.t64 || !B.r || !B.p || !B.Ap || !B.t || !B.st || !B.partials || !B.e || !B.rowc)
     return set_error(HISQ_ENOMEM, "solver workspace");
+  // on request (vector_layout 1), mixed precision with an even number of rhs keeps its inner vectors
+  // interleaved per site, so the Dslash reads each neighbour's nrhs vectors as one block
+  B.il = mixed && nrhs >= 2 && nrhs % 2 == 0 && o.vector_layout == 1;
+  if (B.il) {
+    B.P = nrhs / 2;
+    int spb = 1;
+    while (B.P * spb * 2 <= 256) spb *= 2;
+    B.il_block = B.P * spb;
+  }
+  int prc = plan_update<S>(ctx, B, nrhs);
+  if (prc != HISQ_OK) return prc;
   HISQ_CUDA(cudaMemsetAsync(B.rowc, 0, MAXR * sizeof(unsigned), ctx->stream));
   if (mixed) HISQ_CUDA(cudaMemsetAsync(B.e, 0, (size_t)nrhs * n * 2 * sizeof(float), ctx->stream));
   auto fold = [&]() -> int {
     if (!mixed) return HISQ_OK;
+    if (B.il) {
+      k_fold_il<<<il_grid(ctx, B), B.il_block, 0, ctx->stream>>>(B.x, (float*)B.e, n * B.P, B.P, B.st);
+      HISQ_CUDA(cudaGetLastError());
+      note_launch(ctx);
+      return HISQ_OK;
+    }
     k_fold<<<blas_grid(ctx, nrhs, n), 256, 0, ctx->stream>>>(B.x, (float*)B.e, n, B.st);
     HISQ_CUDA(cudaGetLastError());
     note_launch(ctx);
@@ -448,7 +956,12 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   long long dcalls = 0;
   double dbytes = 0.0;
 
+  constexpr int LANCZOS_CAP = 4096;
+  double* lanczos = (double*)workspace(ctx, "cg_lanczos", 2 * LANCZOS_CAP * sizeof(double));
+  if (!lanczos) return set_error(HISQ_ENOMEM, "solver workspace");
   memset(hst, 0, sizeof(SolverState));
+  hst->lanczos = lanczos;
+  hst->lanczos_cap = LANCZOS_CAP;
   hst->nrhs = nrhs;
   hst->cycle_limit = mixed ? o.reliable_period : o.poll_every;
   for (int q = 0; q < nrhs; ++q) hst->scale[q] = 1.0;
@@ -495,6 +1008,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
   if (o.use_graph) {
     // a cycle's graph depends on the buffers, shapes and per-rhs coefficients it was captured with
     std::string key = "cg/" + std::to_string(sizeof(S)) + "/" + std::to_string(lp) + "/" + std::to_string(nrhs) +
+                      (B.il ? "/il" : "/bl") +
                       "/" + std::to_string(cycle);
     char buf[64];
     for (const void* ptr : {(const void*)B.r, (const void*)B.p, (const void*)B.Ap, (const void*)B.t,
@@ -518,6 +1032,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
       c1.in = B.p;
       c1.nrhs = nrhs;
       c1.rhs_stride = ctx->g.half;
+      c1.interleaved = B.il;
       if ((rc = dslash_launch(ctx, lp, sp, c1)) != HISQ_OK) return rc;
       DslashCall c2 = c1;
       c2.out_parity = 0;
@@ -587,6 +1102,10 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
     last_iter = hst->iter;
     dcalls += 2LL * done_iters;
     dbytes += 2.0 * done_iters * dslash_bytes(ctx, lp, sp, nrhs);
+    if (hst->timeout) {
+      status = set_error(HISQ_ETIMEOUT, "a grid-barrier wait of the CG update ran out at iteration %d", hst->iter);
+      break;
+    }
     if (hst->nonfinite) {
       status = set_error(HISQ_ENONFINITE, "non-finite residual at iteration %d", hst->iter);
       break;
@@ -637,6 +1156,15 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
     stats->seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     stats->dslash_bytes += dbytes;
     stats->dslash_calls += dcalls;
+    // the estimate of A's extreme eigenvalues from rhs 0's Lanczos coefficients
+    const int nl = hst->lanczos_n;
+    stats->lanczos_steps = nl;
+    if (nl > 0) {
+      std::vector<double> ab(2 * (size_t)LANCZOS_CAP);
+      HISQ_CUDA(cudaMemcpy(ab.data(), lanczos, ab.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      if (lanczos_extremes(ab.data(), ab.data() + LANCZOS_CAP, nl, &stats->lambda_min, &stats->lambda_max) != HISQ_OK)
+        stats->lambda_min = stats->lambda_max = 0.0;
+    }
   }
   if (status == HISQ_ENOCONV)
     return set_error(HISQ_ENOCONV, "no convergence in %d iterations (true residual %.3e)", hst->iter, worst);
@@ -1063,6 +1591,11 @@ using namespace hisq;
 
 extern "C" {
 
+int hisq_lanczos_extremes(const double* alpha, const double* beta, int n, double* lmin, double* lmax) {
+  if (!alpha || !beta || !lmin || !lmax || n < 1) return set_error(HISQ_EINVAL, "bad argument");
+  return lanczos_extremes(alpha, beta, n, lmin, lmax);
+}
+
 void hisq_solver_opts_default(hisq_solver_opts* o) {
   if (!o) return;
   o->inner_prec = HISQ_F64;
@@ -1070,6 +1603,7 @@ void hisq_solver_opts_default(hisq_solver_opts* o) {
   o->use_graph = 1;
   o->poll_every = 25;
   o->reliable_prec = HISQ_F64;
+  o->vector_layout = 0;
 }
 
 static int check_solver(hisq_ctx* ctx, const void* x, const void* b, double mass, int maxiter,
@@ -1086,6 +1620,7 @@ static int check_solver(hisq_ctx* ctx, const void* x, const void* b, double mass
     return set_error(HISQ_EINVAL, "reliable-update precision %d must be HISQ_F64 or a resident HISQ_DF64",
                      o->reliable_prec);
   if (o->reliable_period < 1 || o->poll_every < 1) return set_error(HISQ_EINVAL, "periods must be >= 1");
+  if (o->vector_layout != 0 && o->vector_layout != 1) return set_error(HISQ_EINVAL, "vector_layout must be 0 or 1");
   return HISQ_OK;
 }
 

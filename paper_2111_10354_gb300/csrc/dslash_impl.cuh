@@ -1,5 +1,5 @@
-// HISQ even/odd Dslash kernel (the stencil the paper calls "the most performance-critical
-// kernel" of its CG, Sec. 3): for each output site x of one parity,
+// HISQ even/odd Dslash kernel (the stencil that dominates the time of the CG, Sec. 3): for each
+// output site x of one parity,
 //   out(x) = sum_mu [ F_mu(x) in(x+mu) - F_mu(x-mu)^dag in(x-mu)
 //                   + L_mu(x) in(x+3mu) - L_mu(x-3mu)^dag in(x-3mu) ]
 // with staggered phases and the antiperiodic-t sign already folded into F and L.

@@ -10,7 +10,9 @@
 //             FP32      4 planes of float4 + 1 float2 (2 complex entries per float4)
 //             FP16/BF16 2 planes of 16-byte vectors + 1 plane of 4 bytes (4 entries per 16 B)
 //           plane j of block b starts at block base + (sum of earlier chunk sizes) * (V/2).
-//   vectors the boundary layout [rhs][cb][color] of complex<R>, used unchanged inside.
+//   vectors the boundary layout [rhs][cb][color] of complex<R>, or the rhs-interleaved layout
+//           [cb][color][rhs] of the interleaved entry points and of the mixed-precision solver's
+//           multi-RHS inner vectors.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -538,6 +540,7 @@ struct hisq_ctx {
   unsigned load_flags = 0;
   bool links_ready = false;
   int num_sms = 0;
+  int device = 0;                    // CUDA device current at hisq_create (where the links live)
   int autotune = 1;
   std::map<std::string, DevBuf> ws;  // named device workspaces
   std::map<std::string, int> tune;   // kernel key -> block size
@@ -598,6 +601,9 @@ struct DslashCall {
   unsigned* counter = nullptr;
   const int* skip = nullptr;  // device flag: skip the launch's work when set
   int epi = EPI_PLAIN;
+  // vectors in the rhs-interleaved layout [cb][color][rhs] with nrhs vectors per site (one launch
+  // for all of them; rhs_stride is unused), instead of [rhs][cb][color]
+  bool interleaved = false;
 };
 
 // Launch D (link precision lp, spinor precision sp) on ctx->stream.

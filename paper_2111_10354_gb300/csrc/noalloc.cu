@@ -26,9 +26,13 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[HISQ_NOALLOC_SC
 static void* g_scratch_addr[64];
 static std::mutex g_scratch_mutex;
 
-static int scratch_address(void** out) {
+// The array is looked up on the context's own device: the launches run on the context's stream,
+// whose device holds the links, so a copy of the array on any other device would be out of reach.
+static int scratch_address(const hisq_ctx* c, void** out) {
   int dev = -1;
   HISQ_CUDA(cudaGetDevice(&dev));
+  if (dev != c->device)
+    return set_error(HISQ_EINVAL, "the current device %d is not the context's device %d", dev, c->device);
   if (dev < 0 || dev >= 64) return set_error(HISQ_EINVAL, "device ordinal %d outside [0, 64)", dev);
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_addr[dev]) {
@@ -62,7 +66,7 @@ extern "C" int hisq_apply_A_noalloc(hisq_ctx* c, void* out, const void* in, doub
     return set_error(HISQ_EINVAL, "needs %zu bytes of scratch for the odd-site intermediate; the fixed maximum is %zu",
                      need, (size_t)HISQ_NOALLOC_SCRATCH_BYTES);
   void* tmp = nullptr;
-  int rc = scratch_address(&tmp);
+  int rc = scratch_address(c, &tmp);
   if (rc != HISQ_OK) return rc;
   // tmp is written in full by the first launch before the second reads it: nothing to clear.
   DslashCall c1;

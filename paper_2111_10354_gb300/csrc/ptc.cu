@@ -567,6 +567,138 @@ __global__ void k_ptc_wgrad_final(const float* __restrict__ part, int nparts, in
   gW[i] = make_float2((float)((rr + ii) * scale), (float)((ri - ir) * scale));
 }
 
+// ------------------------------------------------------------------ preconditioner apply (inference)
+// The network is linear, so its two layers compose into one operator. With the input r on even sites
+// (zeros on odd sites) and the output read on even sites x:
+//   N(r)(x) = c0 r(x) + sum_{h != 0} T_h phi_h (x),   phi_h(y) = sum_{h' != 0} C[h][h'] (T_h' r)(y)
+// on the odd sites y = x + h, with c0 = sum_a W2[a][0] W1[a][0] and C[h][h'] = sum_a W2[a][h] W1[a][h']
+// (hops h, h' in +x..+t, -x..-t; at an even site only the identity hop of layer 1 sees r, at an odd
+// site only its eight neighbour hops). The 8-channel activation is thereby replaced by the eight
+// mixed transports phi_h of each odd site, written once and read once (an activation of half the
+// lattice that layer 2 needs at x + h only), and each stencil pass reads every fat link once. The
+// weights enter rounded to BF16, as on the tensor-core path that training uses.
+__device__ __forceinline__ cplx<float> bf16c(float2 w) {
+  return {__bfloat162float(__float2bfloat16_rn(w.x)), __bfloat162float(__float2bfloat16_rn(w.y))};
+}
+
+// mix[0] = c0, mix[1 + 8 (h-1) + (h'-1)] = C[h][h'], from W1 [C][1][9] and W2 [1][C][9].
+__global__ void k_ptc_mixing(const float2* __restrict__ w1, const float2* __restrict__ w2, int C, float2* mix) {
+  const int t = threadIdx.x;
+  if (t > 64) return;
+  const int h = t == 0 ? 0 : 1 + (t - 1) / 8, hp = t == 0 ? 0 : 1 + (t - 1) % 8;
+  cplx<float> s = {0.f, 0.f};
+  for (int a = 0; a < C; ++a) cmac(s, bf16c(w2[a * NHOP + h]), bf16c(w1[a * NHOP + hp]));
+  mix[t] = make_float2(s.re, s.im);
+}
+
+// The hop h = 1..8 from a site with coordinates c (lexicographic idx, parity par): neighbour cb, and
+// the link block and cb of the transport's link (F_mu(x) forward, F_mu(x - mu) backward).
+__device__ __forceinline__ int ptc_hop(const PtcGeom& G, const int c[4], int idx, int par, int h, const char** blk,
+                                       int* lcb) {
+  const Geom& g = G.g;
+  const int mu = (h - 1) & 3;
+  const bool fwd = h <= 4;
+  const int nb = neighbour_cb(g, c, idx, mu, fwd ? 1 : -1);
+  *blk = G.fat32 + (size_t)((fwd ? par : 1 - par) * 8 + mu) * G.blk_bytes;
+  *lcb = fwd ? (idx >> 1) : nb;
+  return nb;
+}
+
+// Pass 1, odd sites y: phi_h(y) = sum_h' C[h][h'] (T_h' r)(y), stored as 8 planes [h-1][cb][3].
+__global__ void __launch_bounds__(256) k_ptc_apply_odd(const PtcGeom G, const float2* __restrict__ r,
+                                                       float2* __restrict__ phi, const float2* __restrict__ mix,
+                                                       const int* skip) {
+  if (skip && *skip) return;
+  const Geom& g = G.g;
+  for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.half; cb += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, 1, cb, c);
+    const int idx = lex_index(g, c);
+    cplx<float> acc[8][3];
+#pragma unroll
+    for (int h = 0; h < 8; ++h)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[h][k] = {0.f, 0.f};
+#pragma unroll 1
+    for (int hp = 1; hp <= 8; ++hp) {
+      const char* blk;
+      int lcb;
+      const int nb = ptc_hop(G, c, idx, 1, hp, &blk, &lcb);
+      cplx<float> U[9], v[3], s[3];
+      LinkIO<float>::load(blk, g.half, lcb, U);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 w = __ldg(r + (size_t)nb * 3 + k);
+        v[k] = {w.x, w.y};
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        s[i] = {0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (hp <= 4) cmac(s[i], U[3 * i + j], v[j]);
+          else cmac_conj(s[i], U[3 * j + i], v[j]);
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const float2 m = __ldg(mix + 1 + 8 * h + (hp - 1));
+        const cplx<float> cm = {m.x, m.y};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cmac(acc[h][k], cm, s[k]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 8; ++h)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) phi[((size_t)h * g.half + cb) * 3 + k] = make_float2(acc[h][k].re, acc[h][k].im);
+  }
+}
+
+// Pass 2, even sites x: z(x) = c0 r(x) + sum_h T_h phi_h (x).
+__global__ void __launch_bounds__(256) k_ptc_apply_even(const PtcGeom G, const float2* __restrict__ r,
+                                                        const float2* __restrict__ phi, float2* __restrict__ z,
+                                                        const float2* __restrict__ mix, const int* skip) {
+  if (skip && *skip) return;
+  const Geom& g = G.g;
+  const float2 m0 = __ldg(mix);
+  const cplx<float> c0 = {m0.x, m0.y};
+  for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.half; cb += gridDim.x * blockDim.x) {
+    int c[4];
+    site_coords(g, 0, cb, c);
+    const int idx = lex_index(g, c);
+    cplx<float> acc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 w = __ldg(r + (size_t)cb * 3 + k);
+      acc[k] = {0.f, 0.f};
+      cmac(acc[k], c0, cplx<float>{w.x, w.y});
+    }
+#pragma unroll 4
+    for (int h = 1; h <= 8; ++h) {
+      const char* blk;
+      int lcb;
+      const int nb = ptc_hop(G, c, idx, 0, h, &blk, &lcb);
+      cplx<float> U[9], v[3];
+      LinkIO<float>::load(blk, g.half, lcb, U);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 w = __ldg(phi + ((size_t)(h - 1) * g.half + nb) * 3 + k);
+        v[k] = {w.x, w.y};
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (h <= 4) cmac(acc[i], U[3 * i + j], v[j]);
+          else cmac_conj(acc[i], U[3 * j + i], v[j]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) z[(size_t)cb * 3 + k] = make_float2(acc[k].re, acc[k].im);
+  }
+}
+
 // ------------------------------------------------------------------ small kernels
 // Embed an even-site vector [half][3] into the full lattice (zeros on odd sites).
 __global__ void k_embed_even(const Geom g, const float2* __restrict__ r, float2* __restrict__ full, const int* skip) {
@@ -868,6 +1000,7 @@ struct hisq_ptc {
   int adam_t = 0;
   int tied = 0;  // layer 2 = adjoint of layer 1 (N = B^dag B)
   int* d_err = nullptr;
+  float2* mix = nullptr;  // the composed network's mixing coefficients (65 complex), for the apply
 };
 
 namespace hisq {
@@ -942,18 +1075,23 @@ static int forward_layer(hisq_ptc* P, const float2* in, float2* out, const float
   return HISQ_OK;
 }
 
-// z = N(r) for nvec even-site FP32 vectors (device), using workspaces of the context.
-static int network_apply(hisq_ptc* P, float2* z, const float2* r, int nvec, float2* psi0, float2* psi1,
-                         const int* skip = nullptr) {
+// z = N(r) for nvec even-site FP32 vectors (device), using workspaces of the context: the composed
+// linear operator (k_ptc_mixing, then one stencil pass over odd and one over even sites); phi needs
+// 8 * V/2 * 3 complex64 of workspace.
+static int network_apply(hisq_ptc* P, float2* z, const float2* r, int nvec, float2* phi, const int* skip = nullptr) {
   hisq_ctx* c = P->ctx;
   const size_t nh = (size_t)c->g.half * 3;
+  const PtcGeom G = ptc_geom(c);
+  k_ptc_mixing<<<1, 96, 0, c->stream>>>(P->w1, P->w2, P->C, P->mix);
+  HISQ_CUDA(cudaGetLastError());
+  note_launch(c);
+  int grid = (c->g.half + 255) / 256;
+  if (grid > c->num_sms * 8) grid = c->num_sms * 8;
   for (int v = 0; v < nvec; ++v) {
-    k_embed_even<<<c->num_sms * 4, 256, 0, c->stream>>>(c->g, r + v * nh, psi0, skip);
+    k_ptc_apply_odd<<<grid, 256, 0, c->stream>>>(G, r + v * nh, phi, P->mix, skip);
+    k_ptc_apply_even<<<grid, 256, 0, c->stream>>>(G, r + v * nh, phi, z + v * nh, P->mix, skip);
     HISQ_CUDA(cudaGetLastError());
-    note_launch(c);
-    int rc = forward_layer<1, 8, false>(P, psi0, psi1, P->w1, skip);
-    if (rc == HISQ_OK) rc = forward_layer<8, 1, true>(P, psi1, z + v * nh, P->w2, skip);
-    if (rc != HISQ_OK) return rc;
+    note_launch(c, 2);
   }
   return HISQ_OK;
 }
@@ -1051,6 +1189,7 @@ int hisq_ptc_create(hisq_ptc** out, hisq_ctx* ctx, int channels) {
   if (e == cudaSuccess) e = cudaMemset(P->m1, 0, 4 * nw * 2 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&P->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&P->mix, 65 * sizeof(float2));
   if (e != cudaSuccess) {
     hisq_ptc_destroy(P);
     return cuda_error(e, "ptc buffers");
@@ -1072,6 +1211,7 @@ int hisq_ptc_destroy(hisq_ptc* P) {
   cudaFree(P->g2);
   cudaFree(P->m1);
   cudaFree(P->d_err);
+  cudaFree(P->mix);
   delete P;
   return HISQ_OK;
 }
@@ -1124,10 +1264,9 @@ int hisq_ptc_apply(hisq_ptc* P, float* z, const float* r, int nvec) {
   if (!P->ctx->links_ready) return set_error(HISQ_ENOLINKS, "links not loaded");
   if (!is_device_ptr(z) || !is_device_ptr(r)) return set_error(HISQ_EINVAL, "device vectors only");
   hisq_ctx* c = P->ctx;
-  float2* psi0 = (float2*)workspace(c, "ptc_psi0", (size_t)c->g.V * 3 * sizeof(float2));
-  float2* psi1 = (float2*)workspace(c, "ptc_psi1", (size_t)8 * c->g.V * 3 * sizeof(float2));
-  if (!psi0 || !psi1) return set_error(HISQ_ENOMEM, "ptc workspace");
-  int rc = network_apply(P, (float2*)z, (const float2*)r, nvec, psi0, psi1);
+  float2* phi = (float2*)workspace(c, "ptc_phi", (size_t)8 * c->g.half * 3 * sizeof(float2));
+  if (!phi) return set_error(HISQ_ENOMEM, "ptc workspace");
+  int rc = network_apply(P, (float2*)z, (const float2*)r, nvec, phi);
   if (rc != HISQ_OK) return rc;
   return check_err(P);
 }
@@ -1250,11 +1389,10 @@ int hisq_fcg(hisq_ctx* c, hisq_ptc* P, double* x_user, const double* b_user, dou
   float2* t = (float2*)workspace(c, "fcg_t", n * sizeof(float2));
   float2* z = (float2*)workspace(c, "fcg_z", n * sizeof(float2));
   float2* e = (float2*)workspace(c, "fcg_e", n * sizeof(float2));
-  float2* psi0 = (float2*)workspace(c, "ptc_psi0", (size_t)c->g.V * 3 * sizeof(float2));
-  float2* psi1 = (float2*)workspace(c, "ptc_psi1", (size_t)8 * c->g.V * 3 * sizeof(float2));
+  float2* phi = (float2*)workspace(c, "ptc_phi", (size_t)8 * c->g.half * 3 * sizeof(float2));
   FcgState* st = (FcgState*)workspace(c, "fcg_state", sizeof(FcgState));
   double* partials = (double*)workspace(c, "fcg_partials", 4 * (size_t)c->num_sms * 64 * sizeof(double));
-  if (!x || !b || !rh || !Ax || !t64 || !r || !p || !q || !t || !z || !e || !psi0 || !psi1 || !st || !partials)
+  if (!x || !b || !rh || !Ax || !t64 || !r || !p || !q || !t || !z || !e || !phi || !st || !partials)
     return set_error(HISQ_ENOMEM, "fcg workspace");
   if (xh) HISQ_CUDA(cudaMemcpyAsync(x, x_user, n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
   if (bh) HISQ_CUDA(cudaMemcpyAsync(b, b_user, n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
@@ -1277,7 +1415,7 @@ int hisq_fcg(hisq_ctx* c, hisq_ptc* P, double* x_user, const double* b_user, dou
   auto restart = [&]() -> int {
     k_fcg_reliable<<<gb, 256, 0, c->stream>>>(rh, r, n, st, c->d_counters + 21);
     HISQ_CUDA(cudaGetLastError());
-    int r2 = network_apply(P, z, r, 1, psi0, psi1, &st->done);
+    int r2 = network_apply(P, z, r, 1, phi, &st->done);
     if (r2 != HISQ_OK) return r2;
     k_fcg_pupdate<<<gb, 256, 0, c->stream>>>(p, z, r, half, st, 1, red, c->d_counters + 22);
     HISQ_CUDA(cudaGetLastError());
@@ -1312,7 +1450,7 @@ int hisq_fcg(hisq_ctx* c, hisq_ptc* P, double* x_user, const double* b_user, dou
     if (r2 != HISQ_OK) return r2;
     k_fcg_update<<<gb, 256, 0, c->stream>>>(e, r, p, q, half, st, red, c->d_counters + 24);
     HISQ_CUDA(cudaGetLastError());
-    if ((r2 = network_apply(P, z, r, 1, psi0, psi1, &st->done)) != HISQ_OK) return r2;
+    if ((r2 = network_apply(P, z, r, 1, phi, &st->done)) != HISQ_OK) return r2;
     k_fcg_qz<<<gb, 256, 0, c->stream>>>(q, z, half, st, red, c->d_counters + 25);
     k_fcg_pupdate<<<gb, 256, 0, c->stream>>>(p, z, r, half, st, 0, red, c->d_counters + 22);
     HISQ_CUDA(cudaGetLastError());

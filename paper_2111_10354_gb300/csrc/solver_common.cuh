@@ -19,6 +19,7 @@ struct SolverState {
   double tol2[MAXR];     // (rel_tol * ||b||)^2, target for the true residual squared
   double scale[MAXR];    // true residual = scale * inner residual (mixed precision)
   double rr_true[MAXR];  // last FP64 true residual squared
+  double beta[MAXR];     // this iteration's beta = rr_new / rr (fused update: formed at its grid barrier)
   int rhs_done[MAXR];    // 1: inner-satisfied or verified; frozen (alpha = 0)
   int rhs_conv[MAXR];    // 1: true residual verified below tolerance
   int done;              // the current cycle of iterations is over
@@ -28,7 +29,12 @@ struct SolverState {
   int breakdown;
   int nonfinite;
   int nrhs;
-  int pad;
+  int timeout;           // a bounded grid-barrier wait of the fused update ran out
+  // Lanczos coefficients of rhs 0 (CG's alpha and beta per iteration; alpha = 0 marks a restart of
+  // the search direction), for the estimate of A's extreme eigenvalues: [2][lanczos_cap]
+  double* lanczos;
+  int lanczos_n;
+  int lanczos_cap;
 };
 
 // Reduce NQ per-rhs quantities over a 2D grid (x: sites, y: rhs) into partials[q][rhs][gx];
@@ -84,6 +90,67 @@ __device__ __forceinline__ bool row_reduce(double v, double* partials, size_t ps
   const double t = sum_partials_dyn(partials + (size_t)r * pstride, gridDim.x, red);
   if (threadIdx.x == 0) *total = t;
   return true;
+}
+
+// ------------------------------------------------------------------ grid barrier (one-wave launches)
+// The fused CG update runs as a cooperative launch (every block resident at once) and meets once per
+// launch at a grid barrier: bar[0] counts arrivals, bar[1] is a generation number that the last block
+// to arrive advances after its work. Waiting is bounded: after GRID_WAIT_POLLS polls the block gives up,
+// the caller sets the solver's timeout flag and returns, so a barrier can never hang the GPU.
+constexpr long GRID_WAIT_POLLS = 1L << 22;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Arrive at the barrier (every thread of every block). Returns true in every thread of the last block
+// to arrive; *gen gets the generation this block must see advance before it may go on.
+__device__ __forceinline__ bool grid_arrive(unsigned* bar, unsigned* gen) {
+  __shared__ unsigned s_gen;
+  __shared__ int s_last;
+  __threadfence();  // this thread's writes (partials) become visible to the last block
+  __syncthreads();
+  const bool t0 = threadIdx.x == 0 && threadIdx.y == 0;
+  if (t0) {
+    s_gen = ld_acquire_gpu(bar + 1);
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    s_last = atomicAdd(bar, 1u) == nb - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  *gen = s_gen;
+  return s_last != 0;
+}
+
+// The last block, after its work: reset the count and advance the generation (release).
+__device__ __forceinline__ void grid_release(unsigned* bar) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    bar[0] = 0u;
+    __threadfence();
+    atomicAdd(bar + 1, 1u);
+  }
+  __syncthreads();
+}
+
+// The other blocks: wait (bounded) until the generation has advanced past gen. False on timeout.
+__device__ __forceinline__ bool grid_wait(const unsigned* bar, unsigned gen) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int ok = 0;
+    for (long it = 0; it < GRID_WAIT_POLLS; ++it) {
+      if (ld_acquire_gpu(bar + 1) != gen) {
+        ok = 1;
+        break;
+      }
+      __nanosleep(64);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 template <typename S>

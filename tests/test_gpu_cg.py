@@ -158,3 +158,49 @@ def test_cg_zero_source_and_max_rhs(hisq):
     xs = x.cpu().numpy()
     for r in (0, 17, 63):
         assert oracle.true_residual(L, ff, lf, 0.1, b[r], xs[r]) <= 1e-10
+
+
+@pytest.mark.parametrize("inner,nrhs", [(1, 2), (1, 14), (2, 4), (3, 6)])
+def test_cg_interleaved_inner_vectors_match_blocked(hisq, inner, nrhs):
+    """Mixed-precision multi-RHS solves keep their inner vectors in the boundary layout (vector_layout 0,
+    the default) or interleaved per site (vector_layout 1, even rhs counts). Both are judged by the
+    oracle's true residual, and they take the same number of iterations up to rounding."""
+    import torch
+    L = (8, 10, 12, 14)
+    lat, ff, lf = lattice(hisq, L, 7)
+    b = hin.gen_source(71, lat.half, nrhs)
+    b[1] *= 1e-3  # different scales per rhs
+    its = []
+    for layout in (0, 1):
+        x = torch.zeros((nrhs, lat.half, 3), dtype=torch.complex128, device="cuda")
+        rc, st = lat.cg(x, torch.from_numpy(b).cuda(), 0.02, 1e-10, 5000, nrhs=nrhs, inner_prec=inner,
+                        vector_layout=layout)
+        assert rc == 0 and st["converged"] == 1
+        xs = x.cpu().numpy()
+        for r in range(nrhs):
+            assert oracle.true_residual(L, ff, lf, 0.02, b[r], xs[r]) <= 1e-10, (layout, r)
+        its.append(st["iters"])
+    assert abs(its[0] - its[1]) <= 3, its
+
+
+@pytest.mark.parametrize("inner", [0, 1])
+def test_cg_lanczos_estimate_free_field(hisq, inner):
+    """The solve's Lanczos estimate of A's extreme eigenvalues (from rhs 0's CG coefficients) against the
+    closed-form free-field spectrum at unit links: the largest converges within a few iterations, the
+    smallest as the solve converges. Mixed precision restarts its search direction at every reliable
+    update; its estimate comes from one cycle of 50 iterations and is looser."""
+    import torch
+    from test_oracle_dslash import free_field_eigs
+    L = (8, 8, 8, 8)
+    V = oracle.volume(L)
+    fat = np.broadcast_to(np.eye(3, dtype=np.complex128), (V, 4, 3, 3)).copy()
+    lat = hisq.Lattice(L, precs=(0, 1)).load(fat, -fat / 24)
+    mass = 0.1
+    lam = free_field_eigs(L, mass).ravel()
+    b = hin.gen_source(13, lat.half, 1)
+    x = torch.zeros((1, lat.half, 3), dtype=torch.complex128, device="cuda")
+    rc, st = lat.cg(x, torch.from_numpy(b).cuda(), mass, 1e-12, 5000, inner_prec=inner)
+    assert rc == 0 and st["lanczos_steps"] >= 10
+    tol_max, tol_min = (1e-8, 1e-6) if inner == 0 else (1e-4, 5e-2)
+    assert abs(st["lambda_max"] / lam.max() - 1) < tol_max, (st["lambda_max"], lam.max())
+    assert abs(st["lambda_min"] / lam.min() - 1) < tol_min, (st["lambda_min"], lam.min())

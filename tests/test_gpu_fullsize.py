@@ -1,5 +1,5 @@
 """Parity at the benchmark's full size (48^3x12, links 0.76 GB in FP32 -- far larger than L2), in the launch
-configuration bench.py times: the library's Dslash in FP64/FP32/FP16/double-float, with and without compressed long links,
+configuration bench.py times: the library's Dslash in FP64/FP32/FP16/BF16/double-float, with and without compressed long links,
 against the oracle evaluated one output site at a time on 4096 sampled sites; and the mixed-precision solve
 of the benchmark step judged by the oracle's true residual over the whole lattice. Anti-hermiticity of the
 GPU operator, a property that holds at any size, is checked on the whole lattice too."""
@@ -20,12 +20,12 @@ NSAMPLE = 4096
 def full(hisq):
     fat, lng = hin.gen_links(L, 1001, 0.3, 0.1)  # the benchmark's gauge field
     ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
-    lat = hisq.Lattice(L, precs=(0, 1, 2, 4)).load(fat, lng)
-    comp = hisq.Lattice(L, precs=(0, 1, 2)).compress_long(-1.0 / 24.0).load(fat, lng)
+    lat = hisq.Lattice(L, precs=(0, 1, 2, 3, 4)).load(fat, lng)
+    comp = hisq.Lattice(L, precs=(0, 1, 2, 3)).compress_long(-1.0 / 24.0).load(fat, lng)
     return lat, comp, ff, lf
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 4])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("compressed", [False, True])
 def test_sampled_sites_full_size(full, prec, compressed):
     lat, comp, ff, lf = full

@@ -1,5 +1,5 @@
 """Parity at the Dslash sweep's lattice sizes (32^3x8, 64^3x16, 96^3x24 of the precision workload), in the
-launch configuration the sweep times: the library's Dslash in FP64/FP32/FP16/double-float against the oracle
+launch configuration the sweep times: the library's Dslash in FP64/FP32/FP16/BF16/double-float against the oracle
 evaluated one output site at a time on 2048 sampled sites of each parity, and anti-hermiticity of the GPU
 operator over the whole lattice (<u, D_eo v> = -<D_oe u, v>), a property that holds at any size. Links are
 generated and loaded t-slab by t-slab as in the sweep. 144^3x36 is checked by the sweep itself
@@ -14,7 +14,7 @@ from test_gpu_dslash import TOL, empty_like_prec, from_device, rel_err, to_devic
 pytestmark = pytest.mark.gpu
 
 SIZES = [(32, 32, 32, 8), (64, 64, 64, 16), (96, 96, 96, 24)]
-PRECS = (0, 1, 2, 4)
+PRECS = (0, 1, 2, 3, 4)
 NSAMPLE = 2048
 
 

@@ -12,15 +12,16 @@ import numpy as np
 import pytest
 
 import hisq_inputs as hin
+import oracle
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 2e-6, 2: 5e-3, 3: 5e-3}
+TOL = {0: 1e-12, 1: 2e-6, 2: 5e-3, 3: 5e-3, 4: 1e-12}
 
 
 def _device_vec(torch, src, prec):
     t = torch.from_numpy(np.ascontiguousarray(src))
-    if prec == 0:
+    if prec in (0, 4):
         return t.cuda()
     if prec == 1:
         return t.to(torch.complex64).cuda()
@@ -30,7 +31,7 @@ def _device_vec(torch, src, prec):
 
 def _to_numpy(torch, t, prec):
     t = t.cpu()
-    if prec >= 2:
+    if prec in (2, 3):
         t = torch.view_as_complex(t.float().contiguous())
     return t.to(torch.complex128).numpy()
 
@@ -70,3 +71,28 @@ def test_noalloc_refuses_oversize_and_host_vectors(hisq):
     with pytest.raises(hisq.HisqError) as e:
         hisq.hisq_apply_A_noalloc(lat.ctx, np.zeros_like(xh), xh, 0.1, 0.0, 0, 1)
     assert e.value.code == hisq.HISQ_EINVAL
+
+
+def test_noalloc_16bit_multi_rhs_and_double_float_against_oracle(hisq):
+    """The routes the first test does not reach, checked against the oracle's A directly: 16-bit storage
+    with 8 vectors (its first launch goes through the choice between the CUDA-core and the tensor-core
+    Dslash) and the double-float operator, each called twice in a row on the shared scratch array."""
+    import torch
+    L = (8, 10, 12, 14)
+    fat, lng = hin.gen_links(L, 1234, 0.3, 0.1)
+    lat = hisq.Lattice(L, precs=(0, 2, 3, 4)).load(fat, lng)
+    ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
+    cases = [(2, 8, 0.05, 0.0, 21), (3, 8, 0.03, 0.2, 22), (4, 1, 0.05, 0.3, 23), (4, 2, 0.1, 0.0, 24)]
+    for prec, nrhs, mass, sigma, seed in cases:
+        src = hin.gen_source(seed, lat.half, nrhs)
+        x = _device_vec(torch, src, prec)
+        for call in range(2):
+            y = torch.full_like(x, float("nan"))  # a stale result cannot pass
+            hisq.hisq_apply_A_noalloc(lat.ctx, y, x, mass, sigma, prec, nrhs)
+            torch.cuda.synchronize()
+            got = _to_numpy(torch, y, prec)
+            for r in range(nrhs):
+                ref = oracle.apply_A(L, ff, lf, mass, src[r], sigma=sigma)
+                err = np.linalg.norm((got[r] - ref).ravel()) / np.linalg.norm(ref.ravel())
+                # two Dslash applications: twice the single-operator tolerance
+                assert err <= 2 * TOL[prec], (prec, nrhs, call, r, err)
