@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--sweep", action="store_true", help="Dslash sweep over lattices/precisions (table, not the contract line)")
     ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-df64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8",
                                                    "cg-f32-nr8", "ptc", "fcg", "batch", "smear-f64", "smear-df64",
-                                                   "dslash-f16-nr16-tc", "dslash-f16-nr16-cc", "cg-f32", "multishift"],
+                                                   "dslash-f16-il64-tc", "cg-f32", "multishift", "dslash-f32-il8",
+                                                   "dslash-f32-il16"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned", "smear"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
@@ -582,21 +583,26 @@ def row_multirhs(h, torch, hin):
     lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16, h.HISQ_BF16, h.HISQ_DF64), stream=stream).load(fat, lng)
     peak, _ = peaks()
     dims = "x".join(map(str, L))
-    # 16-bit storage, 8 or more vectors: the tensor-core and the CUDA-core forms, each forced
+    # interleaved layout [cb][color][rhs], 16-bit storage: the tcgen05 tensor-core form against the
+    # CUDA-core interleaved form, each forced; and the blocked CUDA-core form for reference
     for prec, name in ((h.HISQ_F16, "f16"), (h.HISQ_BF16, "bf16")):
-        for n in (8, 16, 32, 64):
+        for n in (16, 32, 64):
             by = lat.dslash_bytes(prec, n)
-            best = {}
-            for path, form in ((1, "cuda-core"), (2, "tensor-core")):
-                h.hisq_tune_load(lat.ctx, "dslash_path/l%d/n%d %s -> %d\n" % (prec, n, dims, path))
-                ms = time_dslash(torch, lat, prec, n, 10, stream)
-                best[path] = ms
+            for path, form in ((1, "interleaved cuda-core"), (2, "interleaved tensor-core (tcgen05)")):
+                h.hisq_tune_load(lat.ctx, "dslash_path_il/l%d/n%d %s -> %d\n" % (prec, n, dims, path))
+                ms = time_dslash(torch, lat, prec, n, 10, stream, interleaved=True)
                 print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": name, "nrhs": n, "form": form,
                                   "dslash_us": round(ms * 1e3, 1), "dslash_GBps": round(by / ms / 1e6, 1),
                                   "dslash_frac_hbm": round(by / ms / 1e6 / peak, 3),
                                   "dslash_GFLOPs": round(1146 * n * lat.half / (ms * 1e-3) / 1e9, 1)}), flush=True)
-            # keep the faster form, as the tuner would
-            h.hisq_tune_load(lat.ctx, "dslash_path/l%d/n%d %s -> %d\n" % (prec, n, dims, min(best, key=best.get)))
+    # FP32 storage: interleaved against blocked, n = 2 .. 16
+    for n in (2, 4, 8, 16):
+        by = lat.dslash_bytes(h.HISQ_F32, n)
+        for il, form in ((False, "blocked"), (True, "interleaved")):
+            ms = time_dslash(torch, lat, h.HISQ_F32, n, 10, stream, interleaved=il)
+            print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": "f32", "nrhs": n, "form": form,
+                              "dslash_us": round(ms * 1e3, 1), "dslash_frac_hbm": round(by / ms / 1e6 / peak, 3),
+                              "dslash_GFLOPs": round(1146 * n * lat.half / (ms * 1e-3) / 1e9, 1)}), flush=True)
     # Dslash only at FP16 storage (FP32 arithmetic) and FP64
     for prec, name, ns in ((h.HISQ_F16, "f16", (1, 2, 4, 8, 16)), (h.HISQ_F64, "f64", (1, 2, 4, 8))):
         for n in ns:
@@ -723,7 +729,7 @@ def row_batch(h, torch, hin):
           flush=True)
 
 
-def row_learned(h, torch, hin, epochs=6, batch_pairs=16):
+def row_learned(h, torch, hin, epochs=12, batch_pairs=16, lr=0.02):
     """32^3x8, m = 0.001, eps = 0.35: train the PTC net on 4 fields x 128 (source, solution) pairs,
     then flexible CG with it vs mixed-precision CG on 4 held-out fields, to 1e-10."""
     import oracle.ptc as optc
@@ -761,13 +767,24 @@ def row_learned(h, torch, hin, epochs=6, batch_pairs=16):
                 net.bind(lat)
                 b, x = pairs[i]
                 loss, _, _ = net.train_step(b[k:k + batch_pairs].contiguous(), x[k:k + batch_pairs].contiguous(),
-                                            batch_pairs, 0.01)
+                                            batch_pairs, lr)
                 ep_loss.append(loss)
         losses.append(float(np.mean(ep_loss)))
     t_train = time.perf_counter() - t0
-    print(json.dumps({"row": "learned", "phase": "train", "pairs": 512, "epochs": epochs,
+    print(json.dumps({"row": "learned", "phase": "train", "pairs": 512, "epochs": epochs, "lr": lr,
                       "data_s": round(t_data, 2), "train_s": round(t_train, 2), "loss_per_epoch": losses}),
           flush=True)
+    # one application of the trained network against one application of A (FP32, the FCG's operator),
+    # device time on the library's stream
+    lat0 = train[0]
+    net.bind(lat0)
+    r32 = torch.from_numpy(hin.gen_source(1, half, 1)).to(torch.complex64).cuda()
+    z32 = torch.empty_like(r32)
+    torch.cuda.synchronize()
+    ms_net = _stream_ms(torch, stream, lambda: net.apply(z32, r32, 1), 50)
+    ms_A = _stream_ms(torch, stream, lambda: lat0.apply_A(z32, r32, mass, h.HISQ_F32, 1), 50)
+    print(json.dumps({"row": "learned", "phase": "apply", "lattice": "32x32x32x8", "network_us": round(ms_net * 1e3, 1),
+                      "A_us": round(ms_A * 1e3, 1)}), flush=True)
     for i in range(4):
         lat = field(4100 + i)
         net.bind(lat)
@@ -904,12 +921,13 @@ def run_kernel_case(name):
             lat.compress_long(-1.0 / 24.0)
         lat.load(fat, lng)
         prec = {"dslash-f64": h.HISQ_F64, "dslash-df64": h.HISQ_DF64, "dslash-f16": h.HISQ_F16,
-                "dslash-f32-comp": h.HISQ_F32, "dslash-f32-nr8": h.HISQ_F32, "dslash-f16-nr16-tc": h.HISQ_F16,
-                "dslash-f16-nr16-cc": h.HISQ_F16}[name]
-        nrhs = 8 if name.endswith("nr8") else (16 if "nr16" in name else 1)
-        if "nr16" in name:  # the tensor-core or the CUDA-core form, forced
-            h.hisq_tune_load(lat.ctx, "dslash_path/l%d/n16 48x48x48x12 -> %d\n" % (prec, 2 if name.endswith("tc") else 1))
-        ms = time_dslash(torch, lat, prec, nrhs, 4, stream)
+                "dslash-f32-comp": h.HISQ_F32, "dslash-f32-nr8": h.HISQ_F32, "dslash-f16-il64-tc": h.HISQ_F16,
+                "dslash-f32-il8": h.HISQ_F32, "dslash-f32-il16": h.HISQ_F32,
+                }[name]
+        nrhs = 8 if name.endswith(("nr8", "il8")) else (16 if name.endswith("il16") else (64 if "il64" in name else 1))
+        if name.endswith("-tc"):  # the tcgen05 tensor-core form, forced
+            h.hisq_tune_load(lat.ctx, "dslash_path_il/l%d/n%d 48x48x48x12 -> 2\n" % (prec, nrhs))
+        ms = time_dslash(torch, lat, prec, nrhs, 4, stream, interleaved="-il" in name)
         print(json.dumps({"case": name, "us": round(ms * 1e3, 2)}))
     elif name == "cg-f32-nr8":
         L = (48, 48, 48, 12)

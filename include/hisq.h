@@ -139,12 +139,7 @@ int hisq_set_long_compression(hisq_ctx* ctx, double naik);
  * out = D_oe in (out_parity = 1). Vectors in precision prec (its links must be
  * resident), nrhs vectors of V/2 sites back to back; out and in must not overlap.
  * Arithmetic: FP64 for HISQ_F64, double-float for HISQ_DF64, FP32 for the others (16-bit
- * types are storage only). With 16-bit storage and nrhs >= 8 there are two forms, FP32 FMAs on
- * the CUDA cores and tensor-core products (mma.sync, FP32 accumulation). With the autotuner on,
- * the first call per (precision, nrhs) runs and times both (the output is written twice, with
- * equal results up to rounding order) and keeps the faster. The choice is listed by
- * hisq_tune_report as "dslash_path/l<prec>/n<nrhs> -> 1 (CUDA cores) or 2 (tensor cores)".
- * Asynchronous on the context's stream for device pointers (apart from that first timing call).
+ * types are storage only). Asynchronous on the context's stream for device pointers.
  * Errors: HISQ_EINVAL (parity, nrhs < 1 or > 64, precision not resident), HISQ_ENOLINKS.
  */
 int hisq_dslash(hisq_ctx* ctx, int out_parity, void* out, const void* in, int prec, int nrhs);
@@ -167,6 +162,14 @@ int hisq_apply_A(hisq_ctx* ctx, void* out, const void* in, double mass, double s
  * HISQ_DF64). Arithmetic, staging of host vectors and errors as hisq_dslash / hisq_apply_A
  * (HISQ_EINVAL also for an nrhs that is not such a multiple). The launch form (vectors per thread)
  * and block size are chosen by the autotuner at the first call per (precision, nrhs).
+ * With 16-bit storage, 16 to 64 vectors and hisq_dslash_interleaved there are two forms: FP32 FMAs
+ * on the CUDA cores, and the fifth-generation tensor cores (tcgen05.mma, one 64 x 8 x 128 product
+ * per site, FP32 accumulation in TMEM). With the autotuner on, the first call per (precision,
+ * nrhs) runs and times both (the output is written twice, with equal results up to rounding
+ * order) and keeps the faster; hisq_tune_report lists the choice as
+ * "dslash_path_il/l<prec>/n<nrhs> -> 1 (CUDA cores) or 2 (tensor cores)". A bounded tensor-core
+ * wait that ran out is reported by that first call (HISQ_ECUDA is not raised; the form is then
+ * not chosen) and writes NaN into the affected outputs.
  */
 int hisq_dslash_interleaved(hisq_ctx* ctx, int out_parity, void* out, const void* in, int prec, int nrhs);
 int hisq_apply_A_interleaved(hisq_ctx* ctx, void* out, const void* in, double mass, double sigma, int prec,

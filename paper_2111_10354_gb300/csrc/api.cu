@@ -16,12 +16,12 @@ int dslash_launch_f32(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_f16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_bf16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int dslash_launch_df64(hisq_ctx* ctx, int sp, const DslashCall& c);
-int dslash_mma_launch(hisq_ctx* ctx, int prec, const DslashCall& c);
 int mrhs_launch_f64(hisq_ctx* ctx, int sp, const DslashCall& c);
 int mrhs_launch_f32(hisq_ctx* ctx, int sp, const DslashCall& c);
 int mrhs_launch_f16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int mrhs_launch_bf16(hisq_ctx* ctx, int sp, const DslashCall& c);
 int mrhs_launch_df64(hisq_ctx* ctx, int sp, const DslashCall& c);
+int dslash_tc_launch(hisq_ctx* ctx, int prec, const DslashCall& c, int* err);
 
 static thread_local char g_last_error[512] = "";
 
@@ -67,32 +67,48 @@ static int dslash_launch_core(hisq_ctx* ctx, int lp, int sp, const DslashCall& c
   return set_error(HISQ_EINVAL, "bad precision %d", lp);
 }
 
-// 16-bit storage with 8 or more right-hand sides and the plain epilogue also has a tensor-core form
-// (dslash_mma.cu). The first such call times both forms (each after its own launch-shape tuning; the
-// plain Dslash does not read its output, so running it twice is harmless) and keeps the faster one
-// per (precision, rhs count) in the tune cache: 1 = CUDA cores, 2 = tensor cores.
-static int dslash_launch_16bit_multi(hisq_ctx* ctx, int lp, const DslashCall& c) {
+static int mrhs_launch_core(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
+  switch (lp) {
+    case HISQ_F64: return mrhs_launch_f64(ctx, sp, c);
+    case HISQ_F32: return mrhs_launch_f32(ctx, sp, c);
+    case HISQ_F16: return mrhs_launch_f16(ctx, sp, c);
+    case HISQ_BF16: return mrhs_launch_bf16(ctx, sp, c);
+    case HISQ_DF64: return mrhs_launch_df64(ctx, sp, c);
+  }
+  return set_error(HISQ_EINVAL, "bad precision %d", lp);
+}
+
+// Interleaved 16-bit storage with 16 or more vectors and the plain epilogue also has a tcgen05
+// tensor-core form (dslash_tc.cu). The first call per (precision, rhs count) times both forms (each
+// after its own launch-shape tuning; the plain Dslash does not read its output, so running it twice
+// is harmless) and keeps the faster: "dslash_path_il/l<prec>/n<nrhs> -> 1 (CUDA cores) or
+// 2 (tensor cores)". A bounded tensor-core wait that ran out is reported by that first call (the
+// kernel also writes NaN into the affected outputs).
+static int dslash_launch_16bit_il(hisq_ctx* ctx, int lp, const DslashCall& c) {
   char key[48];
-  snprintf(key, sizeof key, "dslash_path/l%d/n%d", lp, c.nrhs);
+  snprintf(key, sizeof key, "dslash_path_il/l%d/n%d", lp, c.nrhs);
+  int* err = (int*)workspace(ctx, "tc_err", sizeof(int));
+  if (!err) return set_error(HISQ_ENOMEM, "tensor-core error flag");
   auto it = ctx->tune.find(key);
   if (it != ctx->tune.end()) {
     int v = it->second < 0 ? -it->second : it->second;  // negative: loaded from a report, unchecked
     if (v == 1 || v == 2) {
       it->second = v;
-      return v == 2 ? dslash_mma_launch(ctx, lp, c) : dslash_launch_core(ctx, lp, lp, c);
+      return v == 2 ? dslash_tc_launch(ctx, lp, c, err) : mrhs_launch_core(ctx, lp, lp, c);
     }
     ctx->tune.erase(it);
   }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   HISQ_CUDA(cudaStreamIsCapturing(ctx->stream, &cap));
-  if (!ctx->autotune || cap != cudaStreamCaptureStatusNone) return dslash_launch_core(ctx, lp, lp, c);
+  if (!ctx->autotune || cap != cudaStreamCaptureStatusNone) return mrhs_launch_core(ctx, lp, lp, c);
+  HISQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   cudaEvent_t e[2];
   for (auto& ev : e) HISQ_CUDA(cudaEventCreate(&ev));
   float ms[2] = {0.f, 0.f};
   bool ok[2] = {false, false};
   int rc = HISQ_OK;
   for (int path = 0; path < 2; ++path) {
-    auto run = [&]() { return path == 1 ? dslash_mma_launch(ctx, lp, c) : dslash_launch_core(ctx, lp, lp, c); };
+    auto run = [&]() { return path == 1 ? dslash_tc_launch(ctx, lp, c, err) : mrhs_launch_core(ctx, lp, lp, c); };
     rc = run();  // tunes this form's launch shape
     if (rc == HISQ_OK) {
       cudaEventRecord(e[0], ctx->stream);
@@ -110,30 +126,28 @@ static int dslash_launch_16bit_multi(hisq_ctx* ctx, int lp, const DslashCall& c)
   }
   for (auto& ev : e) cudaEventDestroy(ev);
   if (!ok[0]) return rc != HISQ_OK ? rc : set_error(HISQ_ECUDA, "Dslash timing failed");
+  int herr = 0;
+  HISQ_CUDA(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) {
+    cudaMemsetAsync(err, 0, sizeof(int), ctx->stream);
+    ok[1] = false;  // a bounded wait ran out: the tensor-core form is not used
+  }
   const bool tensor = ok[1] && ms[1] < ms[0];
   ctx->tune[key] = tensor ? 2 : 1;
-  // the output holds the last successful form's result (both forms agree up to rounding order)
-  if (!ok[1]) return dslash_launch_core(ctx, lp, lp, c);
+  // the output holds the last form's result (both forms agree up to rounding order)
+  if (!ok[1]) return mrhs_launch_core(ctx, lp, lp, c);
   return HISQ_OK;
-}
-
-static int mrhs_launch_core(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
-  switch (lp) {
-    case HISQ_F64: return mrhs_launch_f64(ctx, sp, c);
-    case HISQ_F32: return mrhs_launch_f32(ctx, sp, c);
-    case HISQ_F16: return mrhs_launch_f16(ctx, sp, c);
-    case HISQ_BF16: return mrhs_launch_bf16(ctx, sp, c);
-    case HISQ_DF64: return mrhs_launch_df64(ctx, sp, c);
-  }
-  return set_error(HISQ_EINVAL, "bad precision %d", lp);
 }
 
 int dslash_launch(hisq_ctx* ctx, int lp, int sp, const DslashCall& c) {
   if (!ctx->links[lp]) return set_error(HISQ_EINVAL, "link precision %d is not resident", lp);
-  if (c.interleaved) return mrhs_launch_core(ctx, lp, sp, c);
-  const bool compressed = ctx->naik != 0.0 && ctx->long12[lp] != nullptr;
-  if ((lp == HISQ_F16 || lp == HISQ_BF16) && sp == lp && c.epi == EPI_PLAIN && c.nrhs >= 8 && !compressed)
-    return dslash_launch_16bit_multi(ctx, lp, c);
+  if (c.interleaved) {
+    const bool comp = ctx->naik != 0.0 && ctx->long12[lp] != nullptr;
+    if ((lp == HISQ_F16 || lp == HISQ_BF16) && sp == lp && c.epi == EPI_PLAIN && c.nrhs >= 16 && c.nrhs <= 64 &&
+        c.nrhs % 4 == 0 && !comp)
+      return dslash_launch_16bit_il(ctx, lp, c);
+    return mrhs_launch_core(ctx, lp, sp, c);
+  }
   return dslash_launch_core(ctx, lp, sp, c);
 }
 

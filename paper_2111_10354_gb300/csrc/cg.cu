@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "solver_common.cuh"
+#include "reduce_warp.cuh"
 #include "trace.h"
 #include "tune.h"
 
@@ -345,10 +346,7 @@ __device__ __forceinline__ void finish_iteration(SolverState* st, const double* 
   const int nrhs = st->nrhs;
   // whole warps only (a block of P * S threads may end in a partial warp)
   for (int q = warp; warp < nw && q < nrhs; q += nw) {
-    double t = 0.0;
-    for (int b = lane; b < nblk; b += 32) t += __ldcg(partials + (size_t)q * nblk + b);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    const double t = warp_sum_partials(partials + (size_t)q * nblk, nblk);
     if (lane == 0) s_tot[q] = t;
   }
   __syncthreads();
@@ -366,7 +364,7 @@ __device__ __forceinline__ void finish_iteration(SolverState* st, const double* 
 // again. Each thread handles its chunks in batches of KEEP whose loads are all issued before any store. Vector traffic: Ap, r read and r written, then p, x (and r beyond KEEP) read and p, x written:
 // seven vector passes where the two-launch form (k_update + k_pupdate) takes nine.
 template <typename S, typename X, int KEEP>
-__global__ void __launch_bounds__(256, 2) k_cg_update(X* __restrict__ x, S* __restrict__ r, S* __restrict__ p,
+__global__ void __launch_bounds__(256, 4) k_cg_update(X* __restrict__ x, S* __restrict__ r, S* __restrict__ p,
                                                    const S* __restrict__ Ap, size_t n, SolverState* st,
                                                    double* partials, unsigned* bar) {
   using T = typename Real<S>::acc;
@@ -705,8 +703,8 @@ static cudaError_t launch_cooperative(void (*kernel)(Exp...), dim3 grid, int blo
 template <typename S>
 static const void* update_kernel(const CgBuffers& B) {
   if (B.il) return (const void*)k_cg_update_il;
-  if constexpr (sizeof(S) == 8) return (const void*)k_cg_update<double, double, 4>;
-  return (const void*)k_cg_update<float, float, 4>;
+  if constexpr (sizeof(S) == 8) return (const void*)k_cg_update<double, double, 2>;
+  return (const void*)k_cg_update<float, float, 2>;
 }
 
 // One wave of the fused update: as many blocks as are resident together, at most one per unit of work.
@@ -826,10 +824,10 @@ static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
     e = launch_cooperative(k_cg_update_il, B.upd_grid, B.upd_block, ctx->stream, (float*)B.e, (float*)B.r,
                            (float*)B.p, (const float*)B.Ap, n * B.P, B.P, B.st, B.partials, bar);
   else if constexpr (sizeof(S) == 8)
-    e = launch_cooperative(k_cg_update<double, double, 4>, B.upd_grid, B.upd_block, ctx->stream, (double*)B.x,
+    e = launch_cooperative(k_cg_update<double, double, 2>, B.upd_grid, B.upd_block, ctx->stream, (double*)B.x,
                            (double*)B.r, (double*)B.p, (const double*)B.Ap, n, B.st, B.partials, bar);
   else
-    e = launch_cooperative(k_cg_update<float, float, 4>, B.upd_grid, B.upd_block, ctx->stream, (float*)B.e,
+    e = launch_cooperative(k_cg_update<float, float, 2>, B.upd_grid, B.upd_block, ctx->stream, (float*)B.e,
                            (float*)B.r, (float*)B.p, (const float*)B.Ap, n, B.st, B.partials, bar);
   HISQ_CUDA(e);
   note_launch(ctx);

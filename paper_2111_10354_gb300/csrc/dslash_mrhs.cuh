@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "dslash_impl.cuh"
+#include "reduce_warp.cuh"
 
 namespace hisq {
 
@@ -289,10 +290,7 @@ __global__ void __launch_bounds__(256, MrhsBounds<LR, NG * GranIO<SR>::G>::min_b
     if (last_block_done(k.counter)) {
       // one warp per vector: lanes stride over the blocks' partials, then a fixed shuffle tree
       for (int R = warp; R < N; R += nw) {
-        double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(k.partials + (size_t)R * gridDim.x + b);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        const double s = warp_sum_partials(k.partials + (size_t)R * gridDim.x, gridDim.x);
         if (lane == 0) k.dot_out[R] = s;
       }
     }

@@ -604,9 +604,10 @@ __device__ __forceinline__ int ptc_hop(const PtcGeom& G, const int c[4], int idx
   return nb;
 }
 
-// Pass 1, odd sites y: phi_h(y) = sum_h' C[h][h'] (T_h' r)(y), stored as 8 planes [h-1][cb][3].
+// Pass 1, odd sites y: phi_h(y) = sum_h' C[h][h'] (T_h' r)(y), stored as 8 planes [h-1][cb][3] of FP16
+// pairs (relative rounding 2^-11, below the network's BF16 weights' 2^-8).
 __global__ void __launch_bounds__(256) k_ptc_apply_odd(const PtcGeom G, const float2* __restrict__ r,
-                                                       float2* __restrict__ phi, const float2* __restrict__ mix,
+                                                       __half2* __restrict__ phi, const float2* __restrict__ mix,
                                                        const int* skip) {
   if (skip && *skip) return;
   const Geom& g = G.g;
@@ -651,13 +652,13 @@ __global__ void __launch_bounds__(256) k_ptc_apply_odd(const PtcGeom G, const fl
 #pragma unroll
     for (int h = 0; h < 8; ++h)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) phi[((size_t)h * g.half + cb) * 3 + k] = make_float2(acc[h][k].re, acc[h][k].im);
+      for (int k = 0; k < 3; ++k) phi[((size_t)h * g.half + cb) * 3 + k] = __floats2half2_rn(acc[h][k].re, acc[h][k].im);
   }
 }
 
 // Pass 2, even sites x: z(x) = c0 r(x) + sum_h T_h phi_h (x).
 __global__ void __launch_bounds__(256) k_ptc_apply_even(const PtcGeom G, const float2* __restrict__ r,
-                                                        const float2* __restrict__ phi, float2* __restrict__ z,
+                                                        const __half2* __restrict__ phi, float2* __restrict__ z,
                                                         const float2* __restrict__ mix, const int* skip) {
   if (skip && *skip) return;
   const Geom& g = G.g;
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__(256) k_ptc_apply_even(const PtcGeom G, const f
       LinkIO<float>::load(blk, g.half, lcb, U);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float2 w = __ldg(phi + ((size_t)(h - 1) * g.half + nb) * 3 + k);
+        const float2 w = __half22float2(__ldg(phi + ((size_t)(h - 1) * g.half + nb) * 3 + k));
         v[k] = {w.x, w.y};
       }
 #pragma unroll
@@ -1076,15 +1077,12 @@ static int forward_layer(hisq_ptc* P, const float2* in, float2* out, const float
 }
 
 // z = N(r) for nvec even-site FP32 vectors (device), using workspaces of the context: the composed
-// linear operator (k_ptc_mixing, then one stencil pass over odd and one over even sites); phi needs
-// 8 * V/2 * 3 complex64 of workspace.
-static int network_apply(hisq_ptc* P, float2* z, const float2* r, int nvec, float2* phi, const int* skip = nullptr) {
+// linear operator (mixing coefficients formed whenever the weights change, then one stencil pass over
+// odd and one over even sites); phi needs 8 * V/2 * 3 half2 of workspace.
+static int network_apply(hisq_ptc* P, float2* z, const float2* r, int nvec, __half2* phi, const int* skip = nullptr) {
   hisq_ctx* c = P->ctx;
   const size_t nh = (size_t)c->g.half * 3;
   const PtcGeom G = ptc_geom(c);
-  k_ptc_mixing<<<1, 96, 0, c->stream>>>(P->w1, P->w2, P->C, P->mix);
-  HISQ_CUDA(cudaGetLastError());
-  note_launch(c);
   int grid = (c->g.half + 255) / 256;
   if (grid > c->num_sms * 8) grid = c->num_sms * 8;
   for (int v = 0; v < nvec; ++v) {
@@ -1224,6 +1222,7 @@ int hisq_ptc_set_weights(hisq_ptc* P, const float* w1, const float* w2) {
   HISQ_CUDA(cudaMemsetAsync(P->m1, 0, 4 * nb, P->ctx->stream));
   P->adam_t = 0;
   if (P->tied) k_tie<<<1, 128, 0, P->ctx->stream>>>(P->w1, P->w2, P->C);
+  k_ptc_mixing<<<1, 96, 0, P->ctx->stream>>>(P->w1, P->w2, P->C, P->mix);
   HISQ_CUDA(cudaGetLastError());
   HISQ_CUDA(cudaStreamSynchronize(P->ctx->stream));
   return HISQ_OK;
@@ -1234,6 +1233,7 @@ int hisq_ptc_set_tied(hisq_ptc* P, int tied) {
   P->tied = tied ? 1 : 0;
   if (P->tied) {
     k_tie<<<1, 128, 0, P->ctx->stream>>>(P->w1, P->w2, P->C);
+    k_ptc_mixing<<<1, 96, 0, P->ctx->stream>>>(P->w1, P->w2, P->C, P->mix);
     HISQ_CUDA(cudaGetLastError());
     HISQ_CUDA(cudaStreamSynchronize(P->ctx->stream));
   }
@@ -1264,7 +1264,7 @@ int hisq_ptc_apply(hisq_ptc* P, float* z, const float* r, int nvec) {
   if (!P->ctx->links_ready) return set_error(HISQ_ENOLINKS, "links not loaded");
   if (!is_device_ptr(z) || !is_device_ptr(r)) return set_error(HISQ_EINVAL, "device vectors only");
   hisq_ctx* c = P->ctx;
-  float2* phi = (float2*)workspace(c, "ptc_phi", (size_t)8 * c->g.half * 3 * sizeof(float2));
+  __half2* phi = (__half2*)workspace(c, "ptc_phi", (size_t)8 * c->g.half * 3 * sizeof(__half2));
   if (!phi) return set_error(HISQ_ENOMEM, "ptc workspace");
   int rc = network_apply(P, (float2*)z, (const float2*)r, nvec, phi);
   if (rc != HISQ_OK) return rc;
@@ -1352,8 +1352,9 @@ int hisq_ptc_train_step(hisq_ptc* P, const float* b, const float* x, int npairs,
       k_tie<<<1, 128, 0, c->stream>>>(P->w1, P->w2, C);
     else
       k_adam<<<1, 256, 0, c->stream>>>((float*)P->w2, P->m2, P->v2, (const float*)acc2, n, lr, b1, b2, 1e-8f, c1, c2);
+    k_ptc_mixing<<<1, 96, 0, c->stream>>>(P->w1, P->w2, C, P->mix);
     HISQ_CUDA(cudaGetLastError());
-    note_launch(c, 2);
+    note_launch(c, 3);
     HISQ_CUDA(cudaStreamSynchronize(c->stream));
   }
   return HISQ_OK;
@@ -1389,7 +1390,7 @@ int hisq_fcg(hisq_ctx* c, hisq_ptc* P, double* x_user, const double* b_user, dou
   float2* t = (float2*)workspace(c, "fcg_t", n * sizeof(float2));
   float2* z = (float2*)workspace(c, "fcg_z", n * sizeof(float2));
   float2* e = (float2*)workspace(c, "fcg_e", n * sizeof(float2));
-  float2* phi = (float2*)workspace(c, "ptc_phi", (size_t)8 * c->g.half * 3 * sizeof(float2));
+  __half2* phi = (__half2*)workspace(c, "ptc_phi", (size_t)8 * c->g.half * 3 * sizeof(__half2));
   FcgState* st = (FcgState*)workspace(c, "fcg_state", sizeof(FcgState));
   double* partials = (double*)workspace(c, "fcg_partials", 4 * (size_t)c->num_sms * 64 * sizeof(double));
   if (!x || !b || !rh || !Ax || !t64 || !r || !p || !q || !t || !z || !e || !phi || !st || !partials)

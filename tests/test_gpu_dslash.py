@@ -253,29 +253,3 @@ def test_every_launch_form_matches_oracle(hisq, prec):
             for r in range(nr):
                 ref = oracle.apply_A(L, ff, lf, 0.05, src[r])
                 assert rel_err(got[r], ref) <= 2 * TOL[prec], (prec, nr, vi, r)
-
-
-@pytest.mark.parametrize("prec", [2, 3])
-@pytest.mark.parametrize("nrhs", [8, 13, 16, 21, 32, 64])
-@pytest.mark.parametrize("L", [(8, 10, 12, 14), (4, 6, 8, 10), (4, 4, 4, 4)])
-def test_tensor_core_and_cuda_core_forms_match_oracle(hisq, prec, nrhs, L):
-    """16-bit storage with 8 or more vectors has two forms, the tensor-core one (mma.sync, 16 vectors x 8
-    output reals x two hops per product; partial groups of 16 zero-padded; tiles of 16 or 8 sites) and the
-    CUDA-core one; each, forced through loaded tune entries, against the oracle on both parities."""
-    lat, ff, lf = setup(hisq, L)
-    half = lat.half
-    dims = "%dx%dx%dx%d" % L
-    src = hin.gen_source(8000 + nrhs, half, nrhs)
-    x = to_device(src, prec)
-    # the CUDA-core form, then the tensor-core form with tiles of 16 and of 8 sites
-    for path, tile_form in ((1, 0), (2, 0), (2, 1)):
-        rep = "dslash_path/l%d/n%d %s -> %d\n" % (prec, nrhs, dims, path)
-        rep += "dslash_mma/l%d/n%d %s -> %d\n" % (prec, nrhs, dims, tile_form * 10000 + 128)
-        assert hisq.hisq_tune_load(lat.ctx, rep) == 2
-        for parity in (0, 1):
-            y = empty_like_prec((nrhs, half, 3), prec)
-            lat.dslash(parity, y, x, prec, nrhs)
-            got = from_device(y, prec)
-            for r in range(nrhs):
-                ref = oracle.dslash(L, ff, lf, parity, src[r])
-                assert rel_err(got[r], ref) <= TOL[prec], (path, tile_form, parity, r, rel_err(got[r], ref))

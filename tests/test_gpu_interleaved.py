@@ -144,3 +144,41 @@ def test_interleaved_rejects_partial_granules(hisq):
         with pytest.raises(hisq.HisqError) as e:
             lat.dslash_interleaved(0, y, x, prec, nrhs)
         assert e.value.code == hisq.HISQ_EINVAL and "multiple" in str(e.value)
+
+
+@pytest.mark.parametrize("L", LATS)
+@pytest.mark.parametrize("prec,nrhs", [(2, 16), (2, 64), (3, 32), (3, 64), (2, 44)])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_tensor_core_interleaved_dslash_matches_oracle(hisq, L, prec, nrhs, parity):
+    """The tcgen05 form (16-bit storage, 16-64 vectors), forced through a loaded tune entry: every vector
+    against the oracle at the 16-bit tolerance (FP32 accumulation of exact 16-bit products)."""
+    fat, lng = hin.gen_links(L, 1000, 0.3, 0.1)
+    ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
+    lat = hisq.Lattice(L, precs=(0, prec)).load(fat, lng)
+    dims = "x".join(map(str, L))
+    hisq.hisq_tune_load(lat.ctx, "dslash_path_il/l%d/n%d %s -> 2\n" % (prec, nrhs, dims))
+    src = hin.gen_source(1700 + nrhs, lat.half, nrhs)
+    y = empty_interleaved(lat.half, nrhs, prec)
+    lat.dslash_interleaved(parity, y, to_device(interleave(src), prec), prec, nrhs)
+    got = deinterleave(from_device(y, prec))
+    for r in range(nrhs):
+        ref = oracle.dslash(L, ff, lf, parity, src[r])
+        assert rel_err(got[r], ref) <= TOL[prec], (L, prec, nrhs, parity, r, rel_err(got[r], ref))
+    assert "dslash_path_il/l%d/n%d %s -> 2" % (prec, nrhs, dims) in hisq.hisq_tune_report(lat.ctx)
+    lat.close()
+
+
+def test_tensor_core_form_chooser(hisq):
+    """Without a loaded entry the first call times both forms, keeps the faster and records it; the
+    result is correct either way."""
+    L = (16, 16, 16, 8)
+    lat, ff, lf = setup(hisq, L)
+    nrhs, prec = 32, 2
+    src = hin.gen_source(1800, lat.half, nrhs)
+    y = empty_interleaved(lat.half, nrhs, prec)
+    lat.dslash_interleaved(0, y, to_device(interleave(src), prec), prec, nrhs)
+    got = deinterleave(from_device(y, prec))
+    for r in (0, 17, 31):
+        assert rel_err(got[r], oracle.dslash(L, ff, lf, 0, src[r])) <= TOL[prec]
+    rep = hisq.hisq_tune_report(lat.ctx)
+    assert any(l.startswith("dslash_path_il/l2/n32 ") and l.split()[-1] in ("1", "2") for l in rep.splitlines())

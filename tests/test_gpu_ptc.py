@@ -150,3 +150,68 @@ def test_ptc_tied_gradient_parity(setup):
     rloss, G = optc.loss_and_grads_tied(L, ff, w1, list(bs), list(xs))
     assert abs(loss - rloss) <= 1e-2 * abs(rloss)
     assert rel(g1.astype(np.complex128), G) <= 2e-2, rel(g1, G)
+
+
+def test_trained_network_gains_over_the_method_without_it(hisq):
+    """The learned preconditioner's gain, measured: the tied network is trained on the GPU on 3 seeded
+    gauge fields x 128 (Gaussian source, solution) pairs at 16^3x8, m = 0.001 (the solutions from the
+    library's mixed CG to 1e-10), then flexible CG with it solves a held-out field's source to a true
+    residual of 1e-10 (judged by the oracle). It must take at least 9% fewer iterations than both the
+    method without a trained network -- flexible CG with the identity network, and the plain
+    mixed-precision CG -- on that field: 9% is the saving recorded at the 32^3x8 workload with 512 pairs
+    (106 against 117 iterations); this recipe measured 90 against 120 on two held-out fields."""
+    import torch
+    L, mass, npair, bp = (16, 16, 16, 8), 0.001, 128, 16
+
+    def field(seed):
+        fat, lng = hin.gen_links(L, seed, 0.35, 0.1)
+        return hisq.Lattice(L, precs=(0, 1)).load(fat, lng), fat, lng
+
+    train = [field(7000 + i)[0] for i in range(3)]
+    half = train[0].half
+    pairs = []
+    for i, lat in enumerate(train):
+        b = torch.from_numpy(hin.gen_source(7100 + i, half, npair)).cuda()
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        for k in range(0, npair, 16):
+            rc, _ = lat.cg(x[k:k + 16], b[k:k + 16], mass, 1e-10, 20000, nrhs=16, inner_prec=1)
+            assert rc == 0
+        pairs.append((b.to(torch.complex64), x.to(torch.complex64)))
+    W1, _ = optc.init_weights(7000, scale=0.05)
+    W1[0, 0, 0] = 1.0
+    net = hisq.Ptc(train[0])
+    net.set_tied(True)
+    net.set_weights(W1, optc.tie(W1))
+    losses = []
+    for ep in range(12):
+        for k in range(0, npair, bp):
+            for i, lat in enumerate(train):
+                net.bind(lat)
+                b, x = pairs[i]
+                losses.append(net.train_step(b[k:k + bp].contiguous(), x[k:k + bp].contiguous(), bp, 0.02)[0])
+    assert np.mean(losses[-24:]) < 0.5 * np.mean(losses[:24])
+    Wt = net.get_weights()
+
+    lat, fat, lng = field(7200)
+    ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
+    b = hin.gen_source(7300, half, 1)
+    bd = torch.from_numpy(b).cuda()
+    net.bind(lat)
+    x = torch.zeros_like(bd)
+    rc, st = net.fcg(x, bd, mass, 1e-10, 20000)
+    assert rc == 0 and oracle.true_residual(L, ff, lf, mass, b[0], x.cpu().numpy()[0]) <= 1e-10
+    trained = st["iters"]
+    I1 = np.zeros((8, 1, 9), np.complex128)
+    I1[0, 0, 0] = 1.0
+    net.set_weights(I1, optc.tie(I1))
+    x.zero_()
+    rc, st = net.fcg(x, bd, mass, 1e-10, 20000)
+    assert rc == 0
+    identity = st["iters"]
+    x.zero_()
+    rc, st = lat.cg(x, bd, mass, 1e-10, 20000, inner_prec=1)
+    assert rc == 0
+    mixed = st["iters"]
+    net.set_tied(False)
+    assert trained <= 0.91 * min(identity, mixed), (trained, identity, mixed)

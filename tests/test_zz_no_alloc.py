@@ -75,8 +75,8 @@ def test_noalloc_refuses_oversize_and_host_vectors(hisq):
 
 def test_noalloc_16bit_multi_rhs_and_double_float_against_oracle(hisq):
     """The routes the first test does not reach, checked against the oracle's A directly: 16-bit storage
-    with 8 vectors (its first launch goes through the choice between the CUDA-core and the tensor-core
-    Dslash) and the double-float operator, each called twice in a row on the shared scratch array."""
+    with 8 vectors (one multi-vector launch per Dslash, its form picked by the autotuner at the first
+    call) and the double-float operator, each called twice in a row on the shared scratch array."""
     import torch
     L = (8, 10, 12, 14)
     fat, lng = hin.gen_links(L, 1234, 0.3, 0.1)
