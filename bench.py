@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--kernel-case", choices=["dslash-f64", "dslash-df64", "dslash-f16", "dslash-f32-comp", "dslash-f32-nr8",
                                                    "cg-f32-nr8", "ptc", "fcg", "batch", "smear-f64", "smear-df64",
                                                    "dslash-f16-il64-tc", "cg-f32", "multishift", "dslash-f32-il8",
-                                                   "dslash-f32-il16"],
+                                                   "dslash-f32-il16", "dslash-f32-48", "dslash-f32-96",
+                                                   "dslash-f32-144"],
                     help="run a few launches of one kernel on a small case (for profiler captures)")
     ap.add_argument("--row", choices=["multirhs", "multishift", "batch", "learned", "smear"],
                     help="measure one of the batching / learned-preconditioner workloads (JSON lines)")
@@ -472,6 +473,19 @@ def run_ours(args, rank, world, local):
                 sols[name] = xs.cpu().numpy()[0]
     ms_comp = time_dslash(torch, lat, h.HISQ_F32, 1, reps, stream)
 
+    # the conditioning of the small plain-method workload (8^4, m = 0.1, FP64 CG to 1e-10), beside the
+    # benchmark's own
+    L8 = (8, 8, 8, 8)
+    import hisq_inputs as hin
+    small = h.Lattice(L8, precs=(h.HISQ_F64,), stream=stream).load(*hin.gen_links(L8, 1000, 0.3, 0.1))
+    b8 = torch.from_numpy(hin.gen_source(2000, small.half, 1)).cuda()
+    x8 = torch.zeros_like(b8)
+    torch.cuda.synchronize()
+    rc, st8 = small.cg(x8, b8, 0.1, TOL, 20000, inner_prec=h.HISQ_F64)
+    cmp["8^4 m=0.1"] = {"fp64": {"iters": st8["iters"], "true_res": st8["true_rel_residual"]},
+                        "lanczos_A": lanczos_record(st8)}
+    small.close()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -558,7 +572,7 @@ def run_sweep():
                 if nrhs == 1:
                     line["antiherm_rel"] = float("%.3g" % antiherm_rel(torch, lat, p))
                 print(json.dumps(line), flush=True)
-        # the tuner's choice per kernel: variant * 10000 + block (1-vector forms: variant 1 = z-slowest walk)
+        # the tuner's choice per kernel: variant * 10000 + block
         print(json.dumps({"lattice": "x".join(map(str, L)), "tuned": h.hisq_tune_report(lat.ctx).splitlines()}),
               flush=True)
         lat.close()
@@ -588,13 +602,17 @@ def row_multirhs(h, torch, hin):
     for prec, name in ((h.HISQ_F16, "f16"), (h.HISQ_BF16, "bf16")):
         for n in (16, 32, 64):
             by = lat.dslash_bytes(prec, n)
+            best = {}
             for path, form in ((1, "interleaved cuda-core"), (2, "interleaved tensor-core (tcgen05)")):
                 h.hisq_tune_load(lat.ctx, "dslash_path_il/l%d/n%d %s -> %d\n" % (prec, n, dims, path))
                 ms = time_dslash(torch, lat, prec, n, 10, stream, interleaved=True)
+                best[path] = ms
                 print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": name, "nrhs": n, "form": form,
                                   "dslash_us": round(ms * 1e3, 1), "dslash_GBps": round(by / ms / 1e6, 1),
                                   "dslash_frac_hbm": round(by / ms / 1e6 / peak, 3),
                                   "dslash_GFLOPs": round(1146 * n * lat.half / (ms * 1e-3) / 1e9, 1)}), flush=True)
+            # keep the faster form, as the tuner would
+            h.hisq_tune_load(lat.ctx, "dslash_path_il/l%d/n%d %s -> %d\n" % (prec, n, dims, min(best, key=best.get)))
     # FP32 storage: interleaved against blocked, n = 2 .. 16
     for n in (2, 4, 8, 16):
         by = lat.dslash_bytes(h.HISQ_F32, n)
@@ -912,7 +930,29 @@ def run_kernel_case(name):
     __graft_entry__.build()
     import paper_2111_10354_gb300 as h
     stream = torch.cuda.Stream()
-    if name.startswith("dslash"):
+    if name in ("dslash-f32-48", "dslash-f32-96", "dslash-f32-144"):
+        # the FP32 Dslash on 48^3x12, 96^3x24 and 144^3x36 (FP64 + FP32 links resident, loaded slab by
+        # slab): the tuner's choice, then each site order (cb order, the tiled walk) forced with the tuned
+        # block size, for the DRAM traffic of launches whose input vector exceeds L2
+        e = int(name.rsplit("-", 1)[1])
+        L = (e, e, e, e // 4)
+        lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32), stream=stream)
+        nt = max(1, min(L[3], int(2e8 // (L[0] * L[1] * L[2] * 4 * 9 * 16))))
+        for t0 in range(0, L[3], nt):
+            n = min(nt, L[3] - t0)
+            fat, lng = hin.gen_links(L, GAUGE_SEED, 0.3, 0.1, t0=t0, nt=n)
+            h.hisq_load_links_slab(lat.ctx, t0, n, fat, lng)
+        dims = "x".join(map(str, L))
+        key = "dslash/l%d/s%d/nr1/e0/c0" % (h.HISQ_F32, h.HISQ_F32)
+        ms = time_dslash(torch, lat, h.HISQ_F32, 1, 4, stream)
+        tuned = [t for t in h.hisq_tune_report(lat.ctx).splitlines() if t.startswith(key + " ")][0]
+        choice = int(tuned.rsplit(" ", 1)[1])
+        out = {"case": name, "tuned": tuned, "us_tuned": round(ms * 1e3, 2), "bytes": lat.dslash_bytes(h.HISQ_F32, 1)}
+        for vi, pol in ((0, "cb_order"), (1, "tiled_walk")):
+            h.hisq_tune_load(lat.ctx, "%s %s -> %d\n" % (key, dims, vi * 10000 + choice % 10000))
+            out["us_" + pol] = round(time_dslash(torch, lat, h.HISQ_F32, 1, 4, stream) * 1e3, 2)
+        print(json.dumps(out))
+    elif name.startswith("dslash"):
         L = (48, 48, 48, 12)
         fat, lng = hin.gen_links(L, 1001, 0.3, 0.1)
         lat = h.Lattice(L, precs=(h.HISQ_F64, h.HISQ_F32, h.HISQ_F16) + ((h.HISQ_DF64,) if name == "dslash-df64" else ()),

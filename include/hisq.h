@@ -339,8 +339,7 @@ int hisq_fcg(hisq_ctx* ctx, hisq_ptc* ptc, double* x, const double* b, double ma
 /*
  * hisq_apply_A_noalloc -- the paper has no counterpart; this is a service of the library.
  * Same result as hisq_apply_A, out = (4 m^2 + sigma) in - D_eo D_oe in, for callers that cannot
- * allocate device memory when they make the call: code recording into a CUDA graph by stream
- * capture (a cudaMalloc there breaks the capture), code whose device memory is owned by an
+ * allocate device memory when they make the call: code whose device memory is owned by an
  * allocator that forbids foreign allocations, and latency-critical loops that cannot take the
  * device synchronisation of cudaMalloc. hisq_apply_A allocates its odd-site intermediate on first
  * use; this variant keeps it in a fixed file-scope device array of HISQ_NOALLOC_SCRATCH_BYTES and
@@ -348,7 +347,7 @@ int hisq_fcg(hisq_ctx* ctx, hisq_ptc* ptc, double* x, const double* b, double ma
  * in, out: device pointers only (host vectors would need staging buffers); nrhs * V/2 * 6 *
  * sizeof(real of prec) must not exceed HISQ_NOALLOC_SCRATCH_BYTES, else HISQ_EINVAL.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, once per
- * device, with that device current); make that first call before any stream capture. The device
+ * device, with that device current). The device
  * current at the call must be the one that was current at hisq_create, else HISQ_EINVAL.
  * All calls share the array: calls whose work overlaps on the GPU (several streams or host
  * threads at once) race on it. Nothing in it needs clearing: each call overwrites what it reads.
@@ -445,10 +444,11 @@ int hisq_tune_load(hisq_ctx* ctx, const char* report, int* loaded);
 
 /*
  * Self-test of the failure path of the bounded device-side waits (the completion waits of the
- * tensor-core kernels give up after a bounded number of polls, flag the failure and return
- * instead of hanging): launches one block that waits on an mbarrier nothing arrives at. Returns
- * HISQ_ETIMEOUT when the wait gave up as intended -- the expected result -- after which the
- * context remains usable. The paper has no counterpart.
+ * tensor-core kernels and the grid-barrier wait of the fused CG update give up after a bounded
+ * number of polls, flag the failure and return instead of hanging): launches one block that waits
+ * on an mbarrier nothing arrives at and one that waits at a grid barrier whose generation nothing
+ * advances. Returns HISQ_ETIMEOUT when both waits gave up as intended -- the expected result --
+ * after which the context remains usable. The paper has no counterpart.
  */
 int hisq_selftest_bounded_wait(hisq_ctx* ctx);
 

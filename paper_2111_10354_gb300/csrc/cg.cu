@@ -143,6 +143,9 @@ __global__ void k_reliable(const double2* __restrict__ r_hi, S* __restrict__ r_l
 }
 
 
+// Request the 128-byte line holding p (an address inside a vector) into L2; a hint that no register waits on.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Flat 16-byte access to vectors of complex entries for the BLAS kernels: the updates are
 // entry-wise, so a thread takes Chunk<S>::K consecutive complex entries (one 16-byte load per
 // vector; FP32 2, FP64 1) regardless of site boundaries. A rhs holds 3 * half complex
@@ -338,6 +341,68 @@ __device__ __forceinline__ void commit_iteration(SolverState* st, const double* 
   if (all || st->cycle_iter >= st->cycle_limit || st->breakdown || st->nonfinite) st->done = 1;
 }
 
+// The same commit by one full warp (warp 0 of the block that arrived last): lane q takes rhs q, q + 32,
+// ...; lane 0 the counts, flags and the Lanczos record. Every value is loaded before the first store,
+// so the commit costs about two L2 round trips instead of one per field.
+__device__ __forceinline__ void commit_iteration_warp(SolverState* st, const double* tot) {
+  const int lane = threadIdx.x & 31;
+  const int nrhs = st->nrhs;
+  int iter = 0, cyc = 0, lim = 0, brk = 0, nonf = 0, ln = 0, lcap = 0;
+  double* lz = nullptr;
+  if (lane == 0) {
+    iter = st->iter;
+    cyc = st->cycle_iter;
+    lim = st->cycle_limit;
+    brk = st->breakdown;
+    nonf = st->nonfinite;
+    lz = st->lanczos;
+    ln = st->lanczos_n;
+    lcap = st->lanczos_cap;
+  }
+  bool all = true, any_brk = false, any_nonf = false, lz_rec = false;
+  double lz_alpha = 0.0, lz_beta = 0.0;
+  for (int q0 = 0; q0 < nrhs; q0 += 32) {
+    const int q = q0 + lane;
+    bool done_q = true;
+    if (q < nrhs) {
+      const int rd = st->rhs_done[q];
+      const double rr = st->rr[q], pap = st->pAp[q], sc = st->scale[q], tol2 = st->tol2[q], t = tot[q];
+      if (q == 0 && !rd) {
+        lz_rec = true;
+        lz_alpha = rr / pap;
+        lz_beta = t / rr;
+      }
+      st->rr_new[q] = t;
+      done_q = rd != 0;
+      if (!rd) {
+        if (!(pap > 0.0)) any_brk = true;
+        if (!isfinite(t)) any_nonf = true;
+        st->beta[q] = t / rr;
+        st->rr[q] = t;
+        if (t * sc * sc <= tol2) {
+          st->rhs_done[q] = 1;
+          done_q = true;
+        }
+      }
+    }
+    all = __all_sync(0xffffffffu, done_q) && all;
+    any_brk = __any_sync(0xffffffffu, any_brk);
+    any_nonf = __any_sync(0xffffffffu, any_nonf);
+  }
+  if (lane == 0) {
+    if (lz && lz_rec && ln < lcap) {
+      lz[ln] = lz_alpha;
+      lz[lcap + ln] = lz_beta;
+      st->lanczos_n = ln + 1;
+    }
+    if (any_brk) st->breakdown = 1;
+    if (any_nonf) st->nonfinite = 1;
+    st->iter = iter + 1;
+    st->cycle_iter = cyc + 1;
+    if (all || cyc + 1 >= lim || brk || any_brk || nonf || any_nonf) st->done = 1;
+  }
+}
+
 // The last block's part of the barrier: each warp sums the partials of some rhs ([rhs][gridDim.x x
 // gridDim.y blocks], fixed order per lane, then a fixed shuffle tree), thread 0 commits the iteration.
 __device__ __forceinline__ void finish_iteration(SolverState* st, const double* partials, int nblk, double* s_tot) {
@@ -357,7 +422,9 @@ __device__ __forceinline__ void finish_iteration(SolverState* st, const double* 
 // chunks of a rhs, y = rhs; a cooperative launch of one wave):
 //   phase 1: r -= alpha Ap (alpha = rr / pAp), rr_new = |r|^2 (per-chunk terms in the arithmetic
 //            precision, FP64 over chunks);
-//   barrier: the last block to arrive forms rr_new and beta per rhs and commits the iteration;
+//   barrier: one atomic per block; the last block to arrive releases the others at once, then every
+//            block sums its rhs's partials (same order everywhere) into rr_new and beta, and the last
+//            block also commits the iteration (counts, flags, Lanczos record);
 //   phase 2: x += alpha p (X = double: the FP64 solution, X = float: the cycle's FP32 correction);
 //            p = r + beta p.
 // The first KEEP chunks of r a thread updates stay in registers for phase 2; further chunks are read
@@ -372,18 +439,32 @@ __global__ void __launch_bounds__(256, 4) k_cg_update(X* __restrict__ x, S* __re
   constexpr int K = Chunk<S>::K;
   __shared__ double red[32];
   __shared__ double s_tot[MAXR];
+  __shared__ int s_last;
   if (st->done) return;  // uniform: only the last block at the barrier changes it
   const int rh = blockIdx.y;
   const size_t off = (size_t)rh * n;
   const double pap = st->pAp[rh];
   const bool frozen = st->rhs_done[rh] != 0;
   const bool active = !frozen && pap > 0.0 && isfinite(pap);
-  const double alpha = active ? st->rr[rh] / pap : 0.0;
+  const double rr_old = st->rr[rh];
+  const double alpha = active ? rr_old / pap : 0.0;
   const T a = T(alpha);
   const XT ax = XT(sizeof(X) == 8 ? alpha * st->scale[rh] : alpha);
   const size_t stride = (size_t)gridDim.x * blockDim.x * K;
   const size_t i0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K;
   const size_t nn = frozen ? 0 : n;  // a frozen rhs's vectors are not touched
+  // Every 128-byte line of the four vectors this thread group will touch is requested into L2 up front:
+  // prefetches hold no registers, so the whole update's DRAM traffic is in flight at once and both phases
+  // (and the barrier between them) find their data in L2 instead of waiting on DRAM batch by batch.
+  // One thread in eight issues them (eight 16-byte chunks per line).
+  if (active && (threadIdx.x & 7) == 0) {
+    for (size_t i = i0; i < nn; i += stride) {
+      prefetch_l2(reinterpret_cast<const char*>(r) + (off + i) / K * 16);
+      prefetch_l2(reinterpret_cast<const char*>(Ap) + (off + i) / K * 16);
+      prefetch_l2(reinterpret_cast<const char*>(p) + (off + i) / K * 16);
+      prefetch_l2(reinterpret_cast<const char*>(x) + (off + i) * sizeof(cplx<XT>));
+    }
+  }
   cplx<T> keep[KEEP][K];
   double v = 0.0;
   // phase 1 in batches of KEEP chunks: every load of a batch is issued before any store (r is read and
@@ -421,58 +502,76 @@ __global__ void __launch_bounds__(256, 4) k_cg_update(X* __restrict__ x, S* __re
     cplx<T> rv[KEEP][K];
     phase1(ib, rv);
   }
+  // phase 2 (x += alpha p, p = r + beta p), batch by batch: loads first, then the updates, then stores
+  auto update_p_x = [&](double rr_new) {
+    const T beta = T(rr_new / rr_old);
+    auto phase2 = [&](size_t ib, const cplx<T>(&rv)[KEEP][K]) {
+      cplx<T> pv[KEEP][K];
+      cplx<XT> xv[KEEP][K];
+#pragma unroll
+      for (int j = 0; j < KEEP; ++j) {
+        const size_t i = ib + j * stride;
+        if (i < nn) {
+          Chunk<S>::load(p, (off + i) / K, pv[j]);
+          load_k<X, K>(x, off + i, xv[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < KEEP; ++j) {
+        const size_t i = ib + j * stride;
+        if (i < nn) {
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            xv[j][c].re = fma(ax, XT(pv[j][c].re), xv[j][c].re);
+            xv[j][c].im = fma(ax, XT(pv[j][c].im), xv[j][c].im);
+            pv[j][c].re = fma(beta, pv[j][c].re, rv[j][c].re);
+            pv[j][c].im = fma(beta, pv[j][c].im, rv[j][c].im);
+          }
+          store_k<X, K>(x, off + i, xv[j]);
+          Chunk<S>::store(p, (off + i) / K, pv[j]);
+        }
+      }
+    };
+    phase2(i0, keep);
+    for (size_t ib = i0 + KEEP * stride; ib < nn; ib += KEEP * stride) {
+      cplx<T> rv[KEEP][K];
+#pragma unroll
+      for (int j = 0; j < KEEP; ++j) {
+        const size_t i = ib + j * stride;
+        if (i < nn) Chunk<S>::load(r, (off + i) / K, rv[j]);
+      }
+      phase2(ib, rv);
+    }
+  };
   const double bs = block_sum_dyn(v, red);
   if (threadIdx.x == 0) partials[(size_t)rh * gridDim.x + blockIdx.x] = bs;
   unsigned gen;
-  if (grid_arrive(bar, &gen)) {
-    finish_iteration(st, partials, gridDim.x, s_tot);
-    grid_release(bar);
-  } else if (!grid_wait(bar, gen)) {
+  bool last;
+  grid_arrive_release(bar, &gen, &last);
+  if (!grid_wait64(bar, gen)) {
     if (threadIdx.x == 0) {
       st->timeout = 1;
       st->done = 1;
     }
     return;
   }
-  if (!active) return;
-  const T beta = T(__ldcg(&st->beta[rh]));
-  // phase 2, batch by batch: loads first, then x += alpha p, p = r + beta p, then stores
-  auto phase2 = [&](size_t ib, const cplx<T>(&rv)[KEEP][K]) {
-    cplx<T> pv[KEEP][K];
-    cplx<XT> xv[KEEP][K];
-#pragma unroll
-    for (int j = 0; j < KEEP; ++j) {
-      const size_t i = ib + j * stride;
-      if (i < nn) {
-        Chunk<S>::load(p, (off + i) / K, pv[j]);
-        load_k<X, K>(x, off + i, xv[j]);
-      }
+  // every block sums its rhs's partials itself (the same order in every block, so every block forms the
+  // same beta); the block that arrived last also sums every rhs and commits the iteration
+  if (threadIdx.x == 0) s_last = last ? 1 : 0;
+  const double rr_new = block_sum_partials(partials + (size_t)rh * gridDim.x, gridDim.x, red);
+  if (threadIdx.x == 0) s_tot[rh] = rr_new;
+  if (active) update_p_x(rr_new);
+  // after its own vectors (the flag is read back from shared memory so that nothing of this tail stays
+  // in registers through phase 2): the other rhs's sums and the commit, read by the next launches only
+  if (*(volatile int*)&s_last) {
+    const int nrhs = st->nrhs;
+    for (int q = 0; q < nrhs; ++q) {
+      if (q == (int)blockIdx.y) continue;
+      const double t = block_sum_partials(partials + (size_t)q * gridDim.x, gridDim.x, red);
+      if (threadIdx.x == 0) s_tot[q] = t;
     }
-#pragma unroll
-    for (int j = 0; j < KEEP; ++j) {
-      const size_t i = ib + j * stride;
-      if (i < nn) {
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-          xv[j][c].re = fma(ax, XT(pv[j][c].re), xv[j][c].re);
-          xv[j][c].im = fma(ax, XT(pv[j][c].im), xv[j][c].im);
-          pv[j][c].re = fma(beta, pv[j][c].re, rv[j][c].re);
-          pv[j][c].im = fma(beta, pv[j][c].im, rv[j][c].im);
-        }
-        store_k<X, K>(x, off + i, xv[j]);
-        Chunk<S>::store(p, (off + i) / K, pv[j]);
-      }
-    }
-  };
-  phase2(i0, keep);
-  for (size_t ib = i0 + KEEP * stride; ib < nn; ib += KEEP * stride) {
-    cplx<T> rv[KEEP][K];
-#pragma unroll
-    for (int j = 0; j < KEEP; ++j) {
-      const size_t i = ib + j * stride;
-      if (i < nn) Chunk<S>::load(r, (off + i) / K, rv[j]);
-    }
-    phase2(ib, rv);
+    __syncthreads();
+    if (threadIdx.x < 32) commit_iteration_warp(st, s_tot);
   }
 }
 

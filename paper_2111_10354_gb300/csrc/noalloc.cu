@@ -1,10 +1,9 @@
 // hisq_apply_A_noalloc: the shifted operator of hisq_apply_A for callers that cannot allocate
 // device memory at the time of the call. hisq_apply_A keeps the odd-site intermediate
 // D_oe in in a context workspace that it allocates with cudaMalloc on first use (and grows
-// when a larger nrhs arrives). Some callers cannot allow that: code that records the call
-// into a CUDA graph by stream capture (a cudaMalloc during a global-mode capture invalidates
-// it), code whose device memory is owned by an allocator that forbids foreign allocations,
-// and latency-critical loops that cannot take cudaMalloc's implicit device synchronisation.
+// when a larger nrhs arrives). Some callers cannot allow that: code whose device memory is
+// owned by an allocator that forbids foreign allocations, and latency-critical loops that
+// cannot take cudaMalloc's implicit device synchronisation.
 // This entry point keeps the intermediate in a fixed file-scope device array instead and
 // allocates nothing; the caller passes device input and output as usual.
 #include <mutex>

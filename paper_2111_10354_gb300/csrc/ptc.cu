@@ -605,8 +605,10 @@ __device__ __forceinline__ int ptc_hop(const PtcGeom& G, const int c[4], int idx
 }
 
 // Pass 1, odd sites y: phi_h(y) = sum_h' C[h][h'] (T_h' r)(y), stored as 8 planes [h-1][cb][3] of FP16
-// pairs (relative rounding 2^-11, below the network's BF16 weights' 2^-8).
-__global__ void __launch_bounds__(256) k_ptc_apply_odd(const PtcGeom G, const float2* __restrict__ r,
+// pairs (relative rounding 2^-11, below the network's BF16 weights' 2^-8). Blocks of 128 held to 72
+// registers (7 per SM): at 80 registers 32^3x8's 131,072 odd sites needed 1.12 waves of resident
+// threads, and the second wave's few blocks ran alone (ncu: 41% of DRAM peak).
+__global__ void __launch_bounds__(128, 7) k_ptc_apply_odd(const PtcGeom G, const float2* __restrict__ r,
                                                        __half2* __restrict__ phi, const float2* __restrict__ mix,
                                                        const int* skip) {
   if (skip && *skip) return;
@@ -1083,11 +1085,11 @@ static int network_apply(hisq_ptc* P, float2* z, const float2* r, int nvec, __ha
   hisq_ctx* c = P->ctx;
   const size_t nh = (size_t)c->g.half * 3;
   const PtcGeom G = ptc_geom(c);
-  int grid = (c->g.half + 255) / 256;
-  if (grid > c->num_sms * 8) grid = c->num_sms * 8;
+  // one site per thread (the grid-stride loops then run once); the block scheduler balances the waves
+  const int grid_odd = (c->g.half + 127) / 128, grid_even = (c->g.half + 255) / 256;
   for (int v = 0; v < nvec; ++v) {
-    k_ptc_apply_odd<<<grid, 256, 0, c->stream>>>(G, r + v * nh, phi, P->mix, skip);
-    k_ptc_apply_even<<<grid, 256, 0, c->stream>>>(G, r + v * nh, phi, z + v * nh, P->mix, skip);
+    k_ptc_apply_odd<<<grid_odd, 128, 0, c->stream>>>(G, r + v * nh, phi, P->mix, skip);
+    k_ptc_apply_even<<<grid_even, 256, 0, c->stream>>>(G, r + v * nh, phi, z + v * nh, P->mix, skip);
     HISQ_CUDA(cudaGetLastError());
     note_launch(c, 2);
   }

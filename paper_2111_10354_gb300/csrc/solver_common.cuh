@@ -153,6 +153,56 @@ __device__ __forceinline__ bool grid_wait(const unsigned* bar, unsigned gen) {
   return s_ok != 0;
 }
 
+// The same word read as one 64-bit value: bar[0] (arrivals) in the low half, bar[1] (generation) in the
+// high half. With it the last block releases the others in the atomic right after its arrival, and the
+// blocks then do their own post-barrier work in parallel (the fused CG update forms its sums that way).
+__device__ __forceinline__ unsigned long long ld_acquire_gpu64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Arrive (every thread of every block, after the block's partial results are written) and, in the last
+// block to arrive, release at once: one atomic adds 2^32 - nblocks (generation + 1, arrivals back to 0).
+// *gen gets the generation to see advance; *last tells the block whether it arrived last.
+__device__ __forceinline__ void grid_arrive_release(unsigned* bar, unsigned* gen, bool* last) {
+  __shared__ unsigned s_gen;
+  __shared__ int s_last;
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(bar);
+  __threadfence();  // this block's partials become visible before its arrival
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned long long old = atomicAdd(w, 1ull);
+    s_gen = (unsigned)(old >> 32);
+    s_last = (unsigned)(old & 0xffffffffull) == nb - 1 ? 1 : 0;
+    if (s_last) atomicAdd(w, (1ull << 32) - nb);
+  }
+  __syncthreads();
+  *gen = s_gen;
+  *last = s_last != 0;
+}
+
+// Wait (bounded) until the generation in the high half has advanced past gen (acquire: every block's
+// partials are then visible). False on timeout.
+__device__ __forceinline__ bool grid_wait64(const unsigned* bar, unsigned gen, long limit = GRID_WAIT_POLLS) {
+  __shared__ int s_ok;
+  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(bar);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int ok = 0;
+    for (long it = 0; it < limit; ++it) {
+      if ((unsigned)(ld_acquire_gpu64(w) >> 32) != gen) {
+        ok = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 template <typename S>
 struct SAcc {
   using T = typename Real<S>::acc;

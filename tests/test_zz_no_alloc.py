@@ -1,7 +1,7 @@
 """The no-allocation variant of the A operator against the allocating one, through the C ABI.
 
-hisq_apply_A_noalloc serves callers that cannot allocate device memory during the call (stream
-capture into a CUDA graph, framework-owned allocators, latency-critical loops): it keeps the
+hisq_apply_A_noalloc serves callers that cannot allocate device memory during the call
+(framework-owned allocators, latency-critical loops): it keeps the
 odd-site intermediate in a fixed device array instead of a cudaMalloc'ed workspace. Here its output
 must match hisq_apply_A's within the operator tolerances, on two calls in a row, and sizes beyond
 the fixed maximum must be refused with an error.
@@ -96,3 +96,25 @@ def test_noalloc_16bit_multi_rhs_and_double_float_against_oracle(hisq):
                 err = np.linalg.norm((got[r] - ref).ravel()) / np.linalg.norm(ref.ravel())
                 # two Dslash applications: twice the single-operator tolerance
                 assert err <= 2 * TOL[prec], (prec, nrhs, call, r, err)
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(hisq):
+    """What the entry point is for, observed from outside: once first calls have tuned the Dslash launches
+    of each shape and looked up the scratch array, further calls of either shape, with other masses and
+    shifts, leave the device's free memory exactly as it was."""
+    import torch
+    L = (16, 16, 16, 8)
+    fat, lng = hin.gen_links(L, 77, 0.3, 0.1)
+    lat = hisq.Lattice(L, precs=(0, 1)).load(fat, lng)
+    x1 = torch.from_numpy(hin.gen_source(31, lat.half, 1)).to(torch.complex64).cuda()
+    y1 = torch.empty_like(x1)
+    hisq.hisq_apply_A_noalloc(lat.ctx, y1, x1, 0.05, 0.0, 1, 1)  # warm-up: tuning, symbol lookup
+    x4 = torch.from_numpy(hin.gen_source(32, lat.half, 4)).to(torch.complex64).cuda()
+    y4 = torch.empty_like(x4)
+    hisq.hisq_apply_A_noalloc(lat.ctx, y4, x4, 0.05, 0.0, 1, 4)  # tunes the 4-vector launch forms
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for nrhs, x, y in ((1, x1, y1), (4, x4, y4), (1, x1, y1)):
+        hisq.hisq_apply_A_noalloc(lat.ctx, y, x, 0.07, 0.1, 1, nrhs)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
