@@ -310,7 +310,9 @@ int hisq_ptc_set_tied(hisq_ptc* ptc, int tied);
 /* Rebind the network (weights and Adam moments kept) to another context of the same lattice
  * shape, e.g. to train on several gauge fields. */
 int hisq_ptc_bind(hisq_ptc* ptc, hisq_ctx* ctx);
-/* z = N(r) for nvec vectors (device). HISQ_ETIMEOUT if a tensor-core completion wait ran out. */
+/* z = N(r) for nvec even-site FP32 vectors (device), applied in the composed form of the linear
+ * network (one odd-site and one even-site stencil pass on CUDA cores, weights rounded to BF16 as in
+ * training). Asynchronous on the context's stream, like hisq_dslash. */
 int hisq_ptc_apply(hisq_ptc* ptc, float* z, const float* r, int nvec);
 /*
  * Loss = mean over npairs of |N(b_i) - x_i|^2 / |x_i|^2 and its gradients with respect to

@@ -143,9 +143,6 @@ __global__ void k_reliable(const double2* __restrict__ r_hi, S* __restrict__ r_l
 }
 
 
-// Request the 128-byte line holding p (an address inside a vector) into L2; a hint that no register waits on.
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
 // Flat 16-byte access to vectors of complex entries for the BLAS kernels: the updates are
 // entry-wise, so a thread takes Chunk<S>::K consecutive complex entries (one 16-byte load per
 // vector; FP32 2, FP64 1) regardless of site boundaries. A rhs holds 3 * half complex
@@ -453,18 +450,6 @@ __global__ void __launch_bounds__(256, 4) k_cg_update(X* __restrict__ x, S* __re
   const size_t stride = (size_t)gridDim.x * blockDim.x * K;
   const size_t i0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K;
   const size_t nn = frozen ? 0 : n;  // a frozen rhs's vectors are not touched
-  // Every 128-byte line of the four vectors this thread group will touch is requested into L2 up front:
-  // prefetches hold no registers, so the whole update's DRAM traffic is in flight at once and both phases
-  // (and the barrier between them) find their data in L2 instead of waiting on DRAM batch by batch.
-  // One thread in eight issues them (eight 16-byte chunks per line).
-  if (active && (threadIdx.x & 7) == 0) {
-    for (size_t i = i0; i < nn; i += stride) {
-      prefetch_l2(reinterpret_cast<const char*>(r) + (off + i) / K * 16);
-      prefetch_l2(reinterpret_cast<const char*>(Ap) + (off + i) / K * 16);
-      prefetch_l2(reinterpret_cast<const char*>(p) + (off + i) / K * 16);
-      prefetch_l2(reinterpret_cast<const char*>(x) + (off + i) * sizeof(cplx<XT>));
-    }
-  }
   cplx<T> keep[KEEP][K];
   double v = 0.0;
   // phase 1 in batches of KEEP chunks: every load of a batch is issued before any store (r is read and

@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "reduce_warp.cuh"
 
 namespace hisq {
 
@@ -55,7 +56,24 @@ struct DslashKArgs {
   size_t blk12;
   float inv_naik;
   unsigned flags;      // load flags: phases / antiperiodic t (fold signs of compressed links)
+  int walk_zb = 0;     // > 0: output sites walked in tiles of walk_zb z-planes (see walk_cb)
+  int walk_chunk = 0;  // walk_zb * Lx Ly / 2: cb numbers per (tile, t) chunk
+  unsigned long long walk_m_chunk = 0, walk_m_lt = 0;  // 2^64 / walk_chunk and 2^64 / Lt, rounded up
 };
+
+// Output site of walk position w when the sites are walked in tiles of zb z-planes: tile by tile, and in
+// a tile t-slice by t-slice, each (tile, t) chunk being zb * Lx Ly / 2 consecutive cb numbers. In the
+// natural order the +-1 and +-3 t-neighbours of the sites in flight span seven whole t-slices of the
+// input vectors, which exceeds L2 on large lattices (144^3x36 FP32: 250 MB); in the tiled walk they span
+// seven slices of one tile. The neighbours across a tile's z faces are the ones read again. The two
+// divisions are multiplications by rounded-up reciprocals (exact for w < 2^30 and divisors < 2^34).
+__device__ __forceinline__ int walk_cb(const Geom& g, const DslashKArgs& k, int w) {
+  const int q = (int)__umul64hi((unsigned long long)w, k.walk_m_chunk);  // (tile, t) chunk
+  const int o = w - q * k.walk_chunk;
+  const int tile = (int)__umul64hi((unsigned long long)q, k.walk_m_lt);
+  const int t = q - tile * g.L[3];
+  return (tile * k.walk_zb + g.L[2] * t) * (g.half_x * g.L[1]) + o;
+}
 
 // What the compressed-long-link path needs at one site.
 struct Comp12 {
@@ -194,7 +212,8 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
   void* out = (char*)k.out + vbytes;
   const void* y = k.y ? (const void*)((const char*)k.y + vbytes) : nullptr;
 
-  for (int cb = (blockIdx.x * blockDim.x + threadIdx.x) / TS; cb < g.half; cb += gridDim.x * blockDim.x / TS) {
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) / TS; w < g.half; w += gridDim.x * blockDim.x / TS) {
+    const int cb = k.walk_zb ? walk_cb(g, k, w) : w;
     cplx<A> acc[NR][3];
     dslash_site<LR, SR, NR, COMP>(g, k.links, k.blk_bytes, p, cb, in, k.rhs_stride, acc,
                                   Comp12{k.long12, k.blk12, k.inv_naik, k.flags});
@@ -239,9 +258,16 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
       if (threadIdx.x == 0) k.partials[(size_t)R * gridDim.x + blockIdx.x] = s;
     }
     if (last_block_done(k.counter)) {
-      for (int R = 0; R < NR * TS; ++R) {
-        double s = sum_partials_dyn(k.partials + (size_t)R * gridDim.x, gridDim.x, red);
-        if (threadIdx.x == 0) k.dot_out[R] = s;
+      if constexpr (NR * TS == 1) {
+        double s = sum_partials_dyn(k.partials, gridDim.x, red);
+        if (threadIdx.x == 0) k.dot_out[0] = s;
+      } else {
+        // several vectors: one warp per vector sums its partials, the vectors' sums in parallel
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int R = threadIdx.x >> 5; R < NR * TS; R += nw) {
+          const double s = warp_sum_partials(k.partials + (size_t)R * gridDim.x, gridDim.x);
+          if (lane == 0) k.dot_out[R] = s;
+        }
       }
     }
   }

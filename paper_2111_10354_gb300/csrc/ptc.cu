@@ -1268,9 +1268,8 @@ int hisq_ptc_apply(hisq_ptc* P, float* z, const float* r, int nvec) {
   hisq_ctx* c = P->ctx;
   __half2* phi = (__half2*)workspace(c, "ptc_phi", (size_t)8 * c->g.half * 3 * sizeof(__half2));
   if (!phi) return set_error(HISQ_ENOMEM, "ptc workspace");
-  int rc = network_apply(P, (float2*)z, (const float2*)r, nvec, phi);
-  if (rc != HISQ_OK) return rc;
-  return check_err(P);
+  // the composed apply has no tensor-core wait to report: asynchronous on the stream, like hisq_dslash
+  return network_apply(P, (float2*)z, (const float2*)r, nvec, phi);
 }
 
 // Loss (mean over pairs of |N(b)-x|^2/|x|^2) and Wirtinger gradients of both layers for npairs

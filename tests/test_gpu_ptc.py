@@ -158,8 +158,8 @@ def test_trained_network_gains_over_the_method_without_it(hisq):
     library's mixed CG to 1e-10), then flexible CG with it solves a held-out field's source to a true
     residual of 1e-10 (judged by the oracle). It must take at least 9% fewer iterations than both the
     method without a trained network -- flexible CG with the identity network, and the plain
-    mixed-precision CG -- on that field: 9% is the saving recorded at the 32^3x8 workload with 512 pairs
-    (106 against 117 iterations); this recipe measured 90 against 120 on two held-out fields."""
+    mixed-precision CG -- on that field. The bar is conservative: the 32^3x8 workload with 512 pairs saves
+    26% (87 against 117 iterations) and this recipe measured 90 against 120 on two held-out fields."""
     import torch
     L, mass, npair, bp = (16, 16, 16, 8), 0.001, 128, 16
 
