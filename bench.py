@@ -578,6 +578,54 @@ def run_sweep():
         lat.close()
         del lat
         torch.cuda.empty_cache()
+        print(json.dumps(oracle_dslash_timing(hin, L)), flush=True)
+
+
+def host_mem_available() -> float:
+    """Bytes of host memory available now (MemAvailable), 0 if unknown."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return float(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0.0
+
+
+def oracle_dslash_timing(hin, L, reps: int = 5):
+    """The oracle's FP64 Dslash on the sweep lattice L, timed on the host beside the GPU: reps applies on all
+    OpenMP threads and one on a single thread, when the full-lattice host arrays fit in memory (links as
+    generated and as folded: 2304 bytes per site), else the reason it was skipped."""
+    import oracle
+    V = int(np.prod(L))
+    need = 2304.0 * V * 1.25
+    avail = host_mem_available()
+    rec = {"lattice": "x".join(map(str, L)), "oracle_dslash": None}
+    if avail and need > avail:
+        rec["oracle_dslash"] = "skipped: needs %.0f GB of host memory, %.0f GB available" % (need / 1e9, avail / 1e9)
+        return rec
+    oracle.build()
+    fat, lng = hin.gen_links(L, GAUGE_SEED, 0.3, 0.1)
+    ff, lf = oracle.fold_links(L, fat.reshape(-1, 4, 3, 3), lng.reshape(-1, 4, 3, 3))
+    del fat, lng
+    v = hin.gen_source(SOURCE_SEED, V // 2, 1)[0]
+    threads = omp_threads()
+    oracle.dslash(L, ff, lf, 1, v)  # first touch
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.dslash(L, ff, lf, 1, v)
+    dt = (time.perf_counter() - t0) / reps
+    omp_threads(1)
+    t0 = time.perf_counter()
+    oracle.dslash(L, ff, lf, 1, v)
+    dt1 = time.perf_counter() - t0
+    omp_threads(threads)
+    sites = V / 2
+    rec["oracle_dslash"] = {"threads": threads, "cpu_model": cpu_model(), "reps": reps, "s_per_apply": round(dt, 4),
+                            "sites_per_s": float("%.4g" % (sites / dt)), "GB/s": round(sites * 2400 / dt / 1e9, 2),
+                            "single_thread_s_per_apply": round(dt1, 3),
+                            "single_thread_sites_per_s": float("%.4g" % (sites / dt1))}
+    return rec
 
 
 # ----------------------------------------------------------------------------- other workloads
