@@ -430,14 +430,15 @@ def run_ours(args, rank, world, local):
     achieved = bytes_launch / (ms_launch * 1e-3) / 1e9
     launches += 2 * (reps + 3)
 
-    # time-to-1e-10 comparisons (mixed FP32, mixed FP16, plain FP64) at both masses, and the same with the
-    # double-float operator (plain CG, and FP32 inner with double-float reliable updates); every solve is
-    # judged by its true residual
+    # time-to-1e-10 comparisons (mixed FP32, mixed FP16 with FP32 and with FP16 inner vectors, plain FP64)
+    # at both masses, and the same with the double-float operator (plain CG, and FP32 inner with
+    # double-float reliable updates); every solve is judged by its true residual
     cmp = {}
     sols = {}  # GPU solutions at the benchmark's mass, for their error against the oracle's solution
     for m in (0.01, 0.002):
         row = {}
         for name, o in (("mixed_f32", dict(inner_prec=h.HISQ_F32)), ("mixed_f16", dict(inner_prec=h.HISQ_F16)),
+                        ("mixed_f16_spinor16", dict(inner_prec=h.HISQ_F16, spinor_prec=h.HISQ_F16)),
                         ("fp64", dict(inner_prec=h.HISQ_F64)), ("df64", dict(inner_prec=h.HISQ_DF64)),
                         ("mixed_f32_df64_reliable", dict(inner_prec=h.HISQ_F32, reliable_prec=h.HISQ_DF64))):
             xs = torch.zeros_like(b)
@@ -459,7 +460,8 @@ def run_ours(args, rank, world, local):
     lat.compress_long(-1.0 / 24.0).load(fat, lng)
     for m in (0.01, 0.002):
         for name, o in (("mixed_f32_comp12", dict(inner_prec=h.HISQ_F32)),
-                        ("mixed_f16_comp12", dict(inner_prec=h.HISQ_F16))):
+                        ("mixed_f16_comp12", dict(inner_prec=h.HISQ_F16)),
+                        ("mixed_f16_spinor16_comp12", dict(inner_prec=h.HISQ_F16, spinor_prec=h.HISQ_F16))):
             xs = torch.zeros_like(b)
             torch.cuda.synchronize()
             lat.cg(xs, b, m, TOL, 20000, **o)  # first call tunes the compressed kernels
@@ -481,10 +483,26 @@ def run_ours(args, rank, world, local):
     b8 = torch.from_numpy(hin.gen_source(2000, small.half, 1)).cuda()
     x8 = torch.zeros_like(b8)
     torch.cuda.synchronize()
+    small.cg(x8, b8, 0.1, TOL, 20000, inner_prec=h.HISQ_F64)  # first call tunes and captures
+    x8.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     rc, st8 = small.cg(x8, b8, 0.1, TOL, 20000, inner_prec=h.HISQ_F64)
-    cmp["8^4 m=0.1"] = {"fp64": {"iters": st8["iters"], "true_res": st8["true_rel_residual"]},
+    dt8 = time.perf_counter() - t0
+    cmp["8^4 m=0.1"] = {"fp64": {"s": round(dt8, 5), "iters": st8["iters"], "true_res": st8["true_rel_residual"]},
                         "lanczos_A": lanczos_record(st8)}
     small.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle's FP64 CG on the same small workload, on the host's cores
+        import oracle
+        oracle.build()
+        f8, l8 = hin.gen_links(L8, 1000, 0.3, 0.1)
+        ff8, lf8 = oracle.fold_links(L8, f8.reshape(-1, 4, 3, 3), l8.reshape(-1, 4, 3, 3))
+        b8h = hin.gen_source(2000, int(np.prod(L8)) // 2, 1)[0]
+        t0 = time.perf_counter()
+        _, it8 = oracle.cg(L8, ff8, lf8, 0.1, b8h, tol=TOL, maxiter=20000)
+        cmp["8^4 m=0.1"]["oracle_fp64_cpu"] = {"s": round(time.perf_counter() - t0, 5), "iters": it8,
+                                               "cores": omp_threads()}
 
     if rank != 0:
         if dist:

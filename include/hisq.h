@@ -179,9 +179,9 @@ int hisq_apply_A_interleaved(hisq_ctx* ctx, void* out, const void* in, double ma
 typedef struct {
   int inner_prec;       /* HISQ_F64: plain FP64 CG. HISQ_DF64: plain CG with the double-float
                            operator (FP64 vectors and BLAS). HISQ_F32 / F16 / BF16: mixed
-                           precision -- inner CG with links in that precision, FP32 spinors and
-                           arithmetic, FP64 reductions and FP64 solution accumulator, reliable
-                           updates in reliable_prec */
+                           precision -- inner CG with links in that precision, spinors stored as
+                           spinor_prec says, FP32 arithmetic, FP64 reductions and FP64 solution
+                           accumulator, reliable updates in reliable_prec */
   int reliable_period;  /* inner iterations between reliable updates (default 50) */
   int use_graph;        /* 1: capture blocks of iterations in a CUDA graph (default 1) */
   int poll_every;       /* iterations between host convergence polls (default 25) */
@@ -192,6 +192,11 @@ typedef struct {
                            read by the interleaved multi-RHS Dslash). Results agree up to rounding
                            order; the caller's x and b keep the boundary layout either way. On
                            GB300 the default is the faster at every rhs count measured */
+  int spinor_prec;      /* storage of the inner vectors (r, p, Ap and the Dslash intermediate) of a
+                           mixed-precision hisq_cg: HISQ_F32 (default), or 16-bit storage equal to
+                           inner_prec (HISQ_F16 with FP16 links, HISQ_BF16 with BF16 links) with
+                           vector_layout 0; arithmetic stays FP32, reductions and the solution FP64.
+                           Other values, and 16-bit storage in hisq_multishift_cg, give HISQ_EINVAL */
 } hisq_solver_opts;
 
 typedef struct {

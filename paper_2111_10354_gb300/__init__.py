@@ -41,7 +41,8 @@ def HISQ_PREC_BIT(p: int) -> int:
 
 class hisq_solver_opts(ctypes.Structure):
     _fields_ = [("inner_prec", ctypes.c_int), ("reliable_period", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("poll_every", ctypes.c_int), ("reliable_prec", ctypes.c_int), ("vector_layout", ctypes.c_int)]
+                ("poll_every", ctypes.c_int), ("reliable_prec", ctypes.c_int), ("vector_layout", ctypes.c_int),
+                ("spinor_prec", ctypes.c_int)]
 
 
 class hisq_solver_stats(ctypes.Structure):
@@ -268,12 +269,13 @@ def hisq_solver_opts_default() -> hisq_solver_opts:
 
 
 def make_opts(inner_prec: int = HISQ_F64, reliable_period: int = 50, use_graph: bool = True, poll_every: int = 25,
-              reliable_prec: int = HISQ_F64, vector_layout: int = 0):
+              reliable_prec: int = HISQ_F64, vector_layout: int = 0, spinor_prec: int = HISQ_F32):
     o = hisq_solver_opts_default()
     o.inner_prec, o.reliable_period, o.use_graph, o.poll_every = inner_prec, reliable_period, int(use_graph), \
         poll_every
     o.reliable_prec = reliable_prec
     o.vector_layout = vector_layout
+    o.spinor_prec = spinor_prec
     return o
 
 

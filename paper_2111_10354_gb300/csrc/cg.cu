@@ -172,6 +172,53 @@ struct Chunk<double> {
     reinterpret_cast<double2*>(v)[c] = make_double2(o[0].re, o[0].im);
   }
 };
+// 16-bit inner vectors (FP16 or BF16 storage, FP32 arithmetic): four complex entries per 16-byte chunk,
+// converted to FP32 on load and rounded to nearest on store.
+template <>
+struct Chunk<__half> {
+  static constexpr int K = 4;
+  __device__ __forceinline__ static void load(const __half* v, size_t c, cplx<float> o[4]) {
+    const uint4 w = reinterpret_cast<const uint4*>(v)[c];
+    const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[k]));
+      o[k] = {f.x, f.y};
+    }
+  }
+  __device__ __forceinline__ static void store(__half* v, size_t c, const cplx<float> o[4]) {
+    unsigned u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __half2 h = __floats2half2_rn(o[k].re, o[k].im);
+      u[k] = *reinterpret_cast<const unsigned*>(&h);
+    }
+    reinterpret_cast<uint4*>(v)[c] = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+};
+template <>
+struct Chunk<__nv_bfloat16> {
+  static constexpr int K = 4;
+  __device__ __forceinline__ static void load(const __nv_bfloat16* v, size_t c, cplx<float> o[4]) {
+    const uint4 w = reinterpret_cast<const uint4*>(v)[c];
+    const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[k]));
+      o[k] = {f.x, f.y};
+    }
+  }
+  __device__ __forceinline__ static void store(__nv_bfloat16* v, size_t c, const cplx<float> o[4]) {
+    unsigned u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(o[k].re, o[k].im);
+      u[k] = *reinterpret_cast<const unsigned*>(&h);
+    }
+    reinterpret_cast<uint4*>(v)[c] = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+};
+
 // K complex entries starting at entry index e (a multiple of K), in as many chunks of X as needed.
 template <typename X, int K>
 __device__ __forceinline__ void load_k(const X* v, size_t e, cplx<typename Real<X>::acc> o[K]) {
@@ -788,6 +835,7 @@ template <typename S>
 static const void* update_kernel(const CgBuffers& B) {
   if (B.il) return (const void*)k_cg_update_il;
   if constexpr (sizeof(S) == 8) return (const void*)k_cg_update<double, double, 2>;
+  if constexpr (sizeof(S) == 2) return (const void*)k_cg_update<S, float, 1>;  // 4 entries a chunk
   return (const void*)k_cg_update<float, float, 2>;
 }
 
@@ -878,7 +926,7 @@ static int reliable(hisq_ctx* ctx, const CgBuffers& B, int nrhs, int first) {
 // the cycle's correction e in FP32; k_fold adds it to the FP64 x before each reliable update.
 template <typename S>
 static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
-  const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
+  const int sp = Real<S>::prec;
   const size_t n = (size_t)ctx->g.half * 3;
   DslashCall c1;
   c1.out_parity = 1;
@@ -910,6 +958,9 @@ static int iteration(hisq_ctx* ctx, const CgBuffers& B, int lp, int nrhs) {
   else if constexpr (sizeof(S) == 8)
     e = launch_cooperative(k_cg_update<double, double, 2>, B.upd_grid, B.upd_block, ctx->stream, (double*)B.x,
                            (double*)B.r, (double*)B.p, (const double*)B.Ap, n, B.st, B.partials, bar);
+  else if constexpr (sizeof(S) == 2)
+    e = launch_cooperative(k_cg_update<S, float, 1>, B.upd_grid, B.upd_block, ctx->stream, (float*)B.e, (S*)B.r,
+                           (S*)B.p, (const S*)B.Ap, n, B.st, B.partials, bar);
   else
     e = launch_cooperative(k_cg_update<float, float, 2>, B.upd_grid, B.upd_block, ctx->stream, (float*)B.e,
                            (float*)B.r, (float*)B.p, (const float*)B.Ap, n, B.st, B.partials, bar);
@@ -983,8 +1034,9 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
                   hisq_solver_stats* stats) {
   auto t_start = std::chrono::steady_clock::now();
   const int lp = o.inner_prec;
-  const bool mixed = sizeof(S) == 4;  // FP32 inner vectors (FP64 and double-float CG are plain)
-  const int sp = sizeof(S) == 8 ? HISQ_F64 : HISQ_F32;
+  // FP32 or 16-bit inner vectors: mixed precision (FP64 and double-float CG are plain)
+  const bool mixed = sizeof(S) <= 4;
+  const int sp = Real<S>::prec;
   const size_t n = (size_t)ctx->g.half * 3;
   const size_t vb64 = (size_t)nrhs * n * sizeof(double2);
   const size_t vbS = (size_t)nrhs * n * 2 * sizeof(S);
@@ -1009,7 +1061,7 @@ static int run_cg(hisq_ctx* ctx, double2* x, const double2* b, size_t b_stride, 
     return set_error(HISQ_ENOMEM, "solver workspace");
   // on request (vector_layout 1), mixed precision with an even number of rhs keeps its inner vectors
   // interleaved per site, so the Dslash reads each neighbour's nrhs vectors as one block
-  B.il = mixed && nrhs >= 2 && nrhs % 2 == 0 && o.vector_layout == 1;
+  B.il = std::is_same<S, float>::value && nrhs >= 2 && nrhs % 2 == 0 && o.vector_layout == 1;
   if (B.il) {
     B.P = nrhs / 2;
     int spb = 1;
@@ -1686,6 +1738,7 @@ void hisq_solver_opts_default(hisq_solver_opts* o) {
   o->poll_every = 25;
   o->reliable_prec = HISQ_F64;
   o->vector_layout = 0;
+  o->spinor_prec = HISQ_F32;
 }
 
 static int check_solver(hisq_ctx* ctx, const void* x, const void* b, double mass, int maxiter,
@@ -1703,6 +1756,11 @@ static int check_solver(hisq_ctx* ctx, const void* x, const void* b, double mass
                      o->reliable_prec);
   if (o->reliable_period < 1 || o->poll_every < 1) return set_error(HISQ_EINVAL, "periods must be >= 1");
   if (o->vector_layout != 0 && o->vector_layout != 1) return set_error(HISQ_EINVAL, "vector_layout must be 0 or 1");
+  if (o->inner_prec == HISQ_F64 || o->inner_prec == HISQ_DF64) o->spinor_prec = HISQ_F32;  // unused by plain CG
+  const bool sp16 = o->spinor_prec == HISQ_F16 || o->spinor_prec == HISQ_BF16;
+  if (o->spinor_prec != HISQ_F32 && !(sp16 && o->spinor_prec == o->inner_prec && o->vector_layout == 0))
+    return set_error(HISQ_EINVAL, "spinor_prec %d: HISQ_F32, or 16-bit storage equal to inner_prec with "
+                                  "vector_layout 0", o->spinor_prec);
   return HISQ_OK;
 }
 
@@ -1750,6 +1808,10 @@ int hisq_cg(hisq_ctx* ctx, double* x, const double* b, int nrhs, double mass, do
   const long long l0 = ctx->launches;
   if (o.inner_prec == HISQ_F64 || o.inner_prec == HISQ_DF64)
     rc = run_cg<double>(ctx, s.x, s.b, n, nrhs, mass, nullptr, tol.data(), maxiter, o, stats);
+  else if (o.spinor_prec == HISQ_F16)
+    rc = run_cg<__half>(ctx, s.x, s.b, n, nrhs, mass, nullptr, tol.data(), maxiter, o, stats);
+  else if (o.spinor_prec == HISQ_BF16)
+    rc = run_cg<__nv_bfloat16>(ctx, s.x, s.b, n, nrhs, mass, nullptr, tol.data(), maxiter, o, stats);
   else
     rc = run_cg<float>(ctx, s.x, s.b, n, nrhs, mass, nullptr, tol.data(), maxiter, o, stats);
   if (stats) stats->kernel_launches = ctx->launches - l0;
@@ -1764,6 +1826,7 @@ int hisq_multishift_cg(hisq_ctx* ctx, double* x, const double* b, int nshift, co
   if (rc != HISQ_OK) return rc;
   if (nshift < 1 || nshift > MAXR || !shifts || !rel_tol)
     return set_error(HISQ_EINVAL, "nshift %d outside [1, %d] or null shifts/tolerances", nshift, MAXR);
+  if (o.spinor_prec != HISQ_F32) return set_error(HISQ_EINVAL, "multi-shift CG keeps FP32 inner vectors");
   for (int k = 0; k < nshift; ++k)
     if (!(shifts[k] >= 0) || !(rel_tol[k] > 0)) return set_error(HISQ_EINVAL, "shift %d: need sigma >= 0, tol > 0", k);
   if (stats) memset(stats, 0, sizeof *stats);

@@ -204,3 +204,43 @@ def test_cg_lanczos_estimate_free_field(hisq, inner):
     tol_max, tol_min = (1e-8, 1e-6) if inner == 0 else (1e-4, 5e-2)
     assert abs(st["lambda_max"] / lam.max() - 1) < tol_max, (st["lambda_max"], lam.max())
     assert abs(st["lambda_min"] / lam.min() - 1) < tol_min, (st["lambda_min"], lam.min())
+
+
+@pytest.mark.parametrize("prec,nrhs", [(2, 1), (3, 1), (2, 5), (3, 8)])
+def test_cg_16bit_spinor_storage(hisq, prec, nrhs):
+    """Mixed CG with the inner vectors stored in the links' 16-bit format (FP16 or BF16 r, p, Ap and Dslash
+    intermediate; FP32 arithmetic, FP64 reductions, reliable updates and solution): every rhs reaches a true
+    residual of 1e-10, judged by the oracle, at the benchmark mass on rough links, and within twice the
+    iterations of the same solve with FP32 inner vectors."""
+    import torch
+    L = (8, 10, 12, 14)
+    lat, ff, lf = lattice(hisq, L, 17)
+    b = hin.gen_source(170, lat.half, nrhs)
+    bd = torch.from_numpy(b).cuda()
+    its = {}
+    for sp in (1, prec):
+        x = torch.zeros((nrhs, lat.half, 3), dtype=torch.complex128, device="cuda")
+        rc, st = lat.cg(x, bd, 0.01, 1e-10, 5000, nrhs=nrhs, inner_prec=prec, spinor_prec=sp)
+        assert rc == 0 and st["converged"] == 1
+        xs = x.cpu().numpy()
+        for r in range(nrhs):
+            assert oracle.true_residual(L, ff, lf, 0.01, b[r], xs[r]) <= 1e-10, (sp, r)
+        its[sp] = st["iters"]
+    assert its[prec] <= 2 * its[1], its
+
+
+def test_cg_16bit_spinor_storage_errors(hisq):
+    """16-bit inner vectors need links of the same format and the blocked layout, and only hisq_cg has them."""
+    import torch
+    L = (4, 6, 8, 10)
+    lat, ff, lf = lattice(hisq, L, 3, precs=(0, 1, 2, 3))
+    b = torch.from_numpy(hin.gen_source(31, lat.half, 2)).cuda()
+    x = torch.zeros_like(b)
+    for inner, sp, layout in ((1, 2, 0), (2, 3, 0), (3, 2, 0), (2, 2, 1), (2, 0, 0), (2, 4, 0)):
+        with pytest.raises(hisq.HisqError) as e:
+            lat.cg(x, b, 0.1, 1e-10, 100, nrhs=2, inner_prec=inner, spinor_prec=sp, vector_layout=layout)
+        assert e.value.code == hisq.HISQ_EINVAL, (inner, sp, layout)
+    xs = torch.zeros((2, lat.half, 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(hisq.HisqError) as e:
+        lat.multishift_cg(xs, b[:1], [0.0, 0.1], 0.1, [1e-9, 1e-9], 100, inner_prec=2, spinor_prec=2)
+    assert e.value.code == hisq.HISQ_EINVAL
