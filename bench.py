@@ -719,6 +719,14 @@ def row_multirhs(h, torch, hin):
         print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": "f32", "reliable": "df64", "nrhs": n,
                           "cg_s": round(dt, 4), "cg_s_per_rhs": round(dt / n, 4), "cg_iters": st["iters"],
                           "worst_true_res": st["true_rel_residual"]}), flush=True)
+        # FP16 links and FP16 inner vectors (FP32 arithmetic, FP64 reliable updates)
+        o16 = dict(nrhs=n, inner_prec=h.HISQ_F16, spinor_prec=h.HISQ_F16)
+        lat.cg(x, b, 0.01, 1e-10, 5000, **o16)
+        x.zero_()
+        dt, (rc, st) = _timed(torch, lambda: lat.cg(x, b, 0.01, 1e-10, 5000, **o16))
+        print(json.dumps({"row": "multirhs", "lattice": "48x48x48x12", "prec": "f16", "spinor": "f16", "nrhs": n,
+                          "cg_s": round(dt, 4), "cg_s_per_rhs": round(dt / n, 4), "cg_iters": st["iters"],
+                          "worst_true_res": st["true_rel_residual"]}), flush=True)
     # launch forms the tuner chose: key -> variant * 10000 + block (vectors per thread x threads per site)
     print(json.dumps({"row": "multirhs", "tuned": h.hisq_tune_report(lat.ctx).splitlines()}), flush=True)
 

@@ -4,11 +4,12 @@
 // One iteration, for every rhs r at once:
 //   t     = D_oe p                                   (Dslash, odd output)
 //   Ap    = 4m^2 p - D_eo t,  pAp = Re<p, Ap>         (Dslash with fused axpy + FP64 dot)
-//   alpha = rr / pAp;  x += alpha*scale*p;  r -= alpha*Ap;  rr' = |r|^2     (k_update)
-//   beta  = rr' / rr;  p = r + beta*p;  rr = rr'; convergence flags        (k_pupdate)
+//   alpha = rr / pAp;  x += alpha*scale*p;  r -= alpha*Ap;  rr' = |r|^2  \  one cooperative launch
+//   beta  = rr' / rr;  p = r + beta*p;  rr = rr'; convergence flags     /   (k_cg_update)
 // Plain FP64 CG keeps r, p, Ap in FP64 with FP64 links. Mixed precision keeps r, p, Ap in
-// FP32 with links in the inner precision (FP32, FP16 or BF16 storage) and FP32 arithmetic;
-// x, the reductions and the reliable update r = b - A x (FP64 links) stay FP64. Reliable
+// FP32 (or in the links' 16-bit format, on request) with links in the inner precision (FP32,
+// FP16 or BF16 storage) and FP32 arithmetic; x, the reductions and the reliable update
+// r = b - A x (FP64 links) stay FP64. Reliable
 // update (a reading of the paper's "mixed precision" CG, which it names without detail):
 // every reliable_period inner iterations, or as soon as the inner residual says the
 // tolerance is met, recompute the true residual in FP64, rescale it to unit RMS entry,
@@ -234,107 +235,6 @@ __device__ __forceinline__ void store_k(X* v, size_t e, const cplx<typename Real
   for (int j = 0; j < K / KX; ++j) Chunk<X>::store(v, e / KX + j, o + j * KX);
 }
 
-// One CG update, entry-wise: x += alpha*p (X = double: the FP64 solution itself, plain CG; X = float:
-// the FP32 correction e of the current reliable cycle, mixed precision); r -= alpha*Ap;
-// rr_new = |r|^2 with each chunk's term in the arithmetic precision, summed over chunks in FP64.
-// n: complex entries per rhs (3 * half).
-template <typename S, typename X>
-__global__ void __launch_bounds__(256, 6) k_update(X* __restrict__ x, S* __restrict__ r, const S* __restrict__ p, const S* __restrict__ Ap,
-                         size_t n, SolverState* st, double* partials, size_t pstride, unsigned* row_counters) {
-  if (st->done) return;
-  using T = typename Real<S>::acc;
-  using XT = typename Real<X>::acc;
-  constexpr int K = Chunk<S>::K;
-  const int rh = blockIdx.y;
-  const size_t off = (size_t)rh * n;
-  double v[1] = {0.0};
-  const double pap = st->pAp[rh];
-  const bool active = !st->rhs_done[rh] && pap > 0.0 && isfinite(pap);
-  const double alpha = active ? st->rr[rh] / pap : 0.0;
-  const T a = T(alpha);
-  // X = double: x is the solution itself, in true units (alpha * scale); X = float: e is in
-  // inner units and k_fold applies the scale
-  const XT ax = XT(sizeof(X) == 8 ? alpha * st->scale[rh] : alpha);
-  // a frozen rhs's vectors are not touched; the flag is read once (it only changes between launches),
-  // so no load of it sits in front of every iteration's vector loads
-  const bool frozen = st->rhs_done[rh];
-#pragma unroll 2
-  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < (frozen ? 0 : n);
-       i += (size_t)gridDim.x * blockDim.x * K) {
-    cplx<T> pv[K], rv[K], av[K];
-    Chunk<S>::load(p, (off + i) / K, pv);
-    Chunk<S>::load(r, (off + i) / K, rv);
-    if (active) {
-      cplx<XT> xv[K];
-      load_k<X, K>(x, off + i, xv);
-      Chunk<S>::load(Ap, (off + i) / K, av);
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        xv[c].re = fma(ax, XT(pv[c].re), xv[c].re);
-        xv[c].im = fma(ax, XT(pv[c].im), xv[c].im);
-        rv[c].re = fma(-a, av[c].re, rv[c].re);
-        rv[c].im = fma(-a, av[c].im, rv[c].im);
-      }
-      store_k<X, K>(x, off + i, xv);
-      Chunk<S>::store(r, (off + i) / K, rv);
-    }
-    T t = T(0);
-#pragma unroll
-    for (int c = 0; c < K; ++c) t += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
-    v[0] += (double)t;
-  }
-  double tot;
-  if (row_reduce(v[0], partials, pstride, row_counters, &tot) && threadIdx.x == 0) {
-    st->rr_new[rh] = tot;
-    if (!st->rhs_done[rh]) {
-      if (!(pap > 0.0)) st->breakdown = 1;
-      if (!isfinite(tot)) st->nonfinite = 1;
-    }
-  }
-}
-
-// p = r + beta*p with beta = rr_new / rr, entry-wise; then (last block) commit rr, iteration
-// counts, per-rhs inner convergence and the end-of-cycle flag. n: complex entries per rhs.
-template <typename S>
-__global__ void __launch_bounds__(256, 8) k_pupdate(const S* __restrict__ r, S* __restrict__ p, size_t n, SolverState* st,
-                          unsigned* counter) {
-  if (st->done) return;
-  using T = typename Real<S>::acc;
-  constexpr int K = Chunk<S>::K;
-  const int rh = blockIdx.y;
-  const size_t off = (size_t)rh * n;
-  if (!st->rhs_done[rh]) {
-    const T beta = T(st->rr_new[rh] / st->rr[rh]);
-#pragma unroll 2
-    for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * K; i < n;
-         i += (size_t)gridDim.x * blockDim.x * K) {
-      cplx<T> pv[K], rv[K];
-      Chunk<S>::load(p, (off + i) / K, pv);
-      Chunk<S>::load(r, (off + i) / K, rv);
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        pv[c].re = fma(beta, pv[c].re, rv[c].re);
-        pv[c].im = fma(beta, pv[c].im, rv[c].im);
-      }
-      Chunk<S>::store(p, (off + i) / K, pv);
-    }
-  }
-  if (last_block_done(counter) && threadIdx.x == 0) {
-    bool all = true;
-    for (int q = 0; q < st->nrhs; ++q) {
-      if (!st->rhs_done[q]) {
-        st->rr[q] = st->rr_new[q];
-        const double s = st->scale[q];
-        if (st->rr[q] * s * s <= st->tol2[q]) st->rhs_done[q] = 1;
-      }
-      all = all && st->rhs_done[q];
-    }
-    st->iter += 1;
-    st->cycle_iter += 1;
-    if (all || st->cycle_iter >= st->cycle_limit || st->breakdown || st->nonfinite) st->done = 1;
-  }
-}
-
 // End of a mixed-precision cycle: x (FP64) += scale * e (FP32 correction); e = 0.
 __global__ void k_fold(double2* __restrict__ x, float* __restrict__ e, size_t n /* complex per rhs */,
                        const SolverState* st) {
@@ -360,7 +260,7 @@ __global__ void k_new_cycle(SolverState* st) {
 // ------------------------------------------------------------------ fused update (one launch per iteration)
 // Commit of one iteration by the last block at the fused update's grid barrier (one thread): tot[q] =
 // |r_q|^2 after the r update. Forms beta = rr_new / rr, commits rr, per-rhs inner convergence, the
-// iteration counts and the end-of-cycle flag (the bookkeeping of k_update's and k_pupdate's last blocks).
+// iteration counts and the end-of-cycle flag.
 __device__ __forceinline__ void commit_iteration(SolverState* st, const double* tot) {
   if (st->lanczos && !st->rhs_done[0] && st->lanczos_n < st->lanczos_cap) {
     st->lanczos[st->lanczos_n] = st->rr[0] / st->pAp[0];                      // alpha
@@ -473,7 +373,7 @@ __device__ __forceinline__ void finish_iteration(SolverState* st, const double* 
 //            p = r + beta p.
 // The first KEEP chunks of r a thread updates stay in registers for phase 2; further chunks are read
 // again. Each thread handles its chunks in batches of KEEP whose loads are all issued before any store. Vector traffic: Ap, r read and r written, then p, x (and r beyond KEEP) read and p, x written:
-// seven vector passes where the two-launch form (k_update + k_pupdate) takes nine.
+// seven vector passes where an x/r update launch and a separate p update launch take nine.
 template <typename S, typename X, int KEEP>
 __global__ void __launch_bounds__(256, 4) k_cg_update(X* __restrict__ x, S* __restrict__ r, S* __restrict__ p,
                                                    const S* __restrict__ Ap, size_t n, SolverState* st,

@@ -1,4 +1,5 @@
-// Warp-level sum of per-block partial results, shared by the multi-RHS Dslash and the CG updates.
+// Sums of per-block partial results by one warp or by a whole block, in a fixed order: shared by the
+// multi-RHS Dslash epilogues and the CG updates.
 #pragma once
 #include <cuda_runtime.h>
 

@@ -39,3 +39,34 @@ def test_pointers():
     assert h._ptr(t).value == t.data_ptr()
     with pytest.raises(TypeError):
         h._ptr("not an array")
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structs against the C header, compiled by the host compiler: the size of each
+    struct and the offset of every field the binding declares (a field added on one side only would
+    shift everything after it)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"hisq_solver_opts": h.hisq_solver_opts, "hisq_solver_stats": h.hisq_solver_stats,
+               "hisq_smear_coeffs": h.hisq_smear_coeffs}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "hisq.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
