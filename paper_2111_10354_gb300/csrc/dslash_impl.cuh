@@ -57,6 +57,7 @@ struct DslashKArgs {
   float inv_naik;
   unsigned flags;      // load flags: phases / antiperiodic t (fold signs of compressed links)
   int walk_zb = 0;     // > 0: output sites walked in tiles of walk_zb z-planes (see walk_cb)
+  int prefetch = 0;    // 1 (8-vector forms): each hop requests the next hop's vectors and link ahead
   int walk_chunk = 0;  // walk_zb * Lx Ly / 2: cb numbers per (tile, t) chunk
   unsigned long long walk_m_chunk = 0, walk_m_lt = 0;  // 2^64 / walk_chunk and 2^64 / Lt, rounded up
 };
@@ -83,12 +84,35 @@ struct Comp12 {
   unsigned flags;
 };
 
+// Requests for data a later hop reads: the vectors into L1, the (streamed, evict-first) link into L2.
+// Hints only: nothing waits on them and no register receives data.
+__device__ __forceinline__ void prefetch_l1(const void* a) { asm volatile("prefetch.global.L1 [%0];" ::"l"(a)); }
+__device__ __forceinline__ void prefetch_l2(const void* a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
+// The link of site cb in block blk, plane by plane as LinkIO reads it (FP32: 4 x 16 B + 8 B; 16-bit:
+// 2 x 16 B + 4 B); the 8-vector forms that prefetch exist for these precisions only.
+template <typename LR>
+__device__ __forceinline__ void prefetch_link(const char* blk, int half, int cb) {
+  if constexpr (std::is_same<LR, float>::value) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) prefetch_l2(blk + ((size_t)j * half + cb) * 16);
+    prefetch_l2(blk + (size_t)64 * half + (size_t)cb * 8);
+  } else if constexpr (sizeof(LR) == 2) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) prefetch_l2(blk + ((size_t)j * half + cb) * 16);
+    prefetch_l2(blk + (size_t)32 * half + (size_t)cb * 4);
+  }
+}
+
 // The 16 hopping terms at output site cb (parity p) for NR vectors: acc[r][i] = (D in_r)(x)_i.
 // links: the 16 blocks of one lattice in the link precision; in: NR vectors rhs_stride sites apart.
+// pf (8-vector forms): while a hop computes, the next hop's NR vectors are requested into L1 and its
+// link into L2, so the next hop's loads do not wait on DRAM (16 warps per SM at 128 registers leave
+// little else to cover that latency).
 template <typename LR, typename SR, int NR, bool COMP = false>
 __device__ __forceinline__ void dslash_site(const Geom& g, const char* links, size_t blk_bytes, int p, int cb,
                                             const void* in, size_t rhs_stride,
-                                            cplx<typename Real<LR>::acc> (&acc)[NR][3], const Comp12& cz = Comp12{}) {
+                                            cplx<typename Real<LR>::acc> (&acc)[NR][3], const Comp12& cz = Comp12{},
+                                            bool pf = false) {
   using A = typename Real<LR>::acc;
   using SA = typename Real<SR>::acc;
   const char* fwd = links + (size_t)(p * 8) * blk_bytes;        // blocks of parity p
@@ -116,6 +140,15 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const char* links, si
       // forward hop: + W_mu(x) in(x + hop mu)
       {
         const int nb = neighbour_cb(g, c, idx, mu, +hop);
+        if constexpr (NR >= 8 && sizeof(LR) < 8) {
+          if (pf) {  // the backward hop of this (mu, kind)
+            constexpr size_t VB = 6 * sizeof(SR);  // bytes of one vector at one site
+            const int nbb = neighbour_cb(g, c, idx, mu, -hop);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) prefetch_l1((const char*)in + ((size_t)r * rhs_stride + nbb) * VB);
+            if (!(COMP && kind == 1)) prefetch_link<LR>(blk_b, g.half, nbb);
+          }
+        }
         cplx<A> U[9];
         if constexpr (COMP && sizeof(LR) < 8) {
           if (kind == 1) {
@@ -142,6 +175,16 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const char* links, si
       // backward hop: - W_mu(x - hop mu)^dag in(x - hop mu)
       {
         const int nb = neighbour_cb(g, c, idx, mu, -hop);
+        if constexpr (NR >= 8 && sizeof(LR) < 8) {
+          if (pf && (kind == 0 || mu < 3)) {  // the forward hop of the next (mu, kind)
+            constexpr size_t VB = 6 * sizeof(SR);
+            const int kn = kind ^ 1, mn = kind == 0 ? mu : mu + 1;
+            const int nbn = neighbour_cb(g, c, idx, mn, kn == 0 ? 1 : 3);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) prefetch_l1((const char*)in + ((size_t)r * rhs_stride + nbn) * VB);
+            if (!(COMP && kn == 1)) prefetch_link<LR>(fwd + (size_t)(kn * 4 + mn) * blk_bytes, g.half, cb);
+          }
+        }
         cplx<A> U[9];
         if constexpr (COMP && sizeof(LR) < 8) {
           if (kind == 1) {
@@ -216,7 +259,7 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
     const int cb = k.walk_zb ? walk_cb(g, k, w) : w;
     cplx<A> acc[NR][3];
     dslash_site<LR, SR, NR, COMP>(g, k.links, k.blk_bytes, p, cb, in, k.rhs_stride, acc,
-                                  Comp12{k.long12, k.blk12, k.inv_naik, k.flags});
+                                  Comp12{k.long12, k.blk12, k.inv_naik, k.flags}, k.prefetch != 0);
 
 #pragma unroll
     for (int r = 0; r < NR; ++r) {

@@ -35,7 +35,7 @@ inline void set_walk(const hisq_ctx* ctx, DslashKArgs& a, int zb) {
 
 // One launch form: NR vectors per thread, TS threads per site (NR * TS vectors per launch); WALK: the
 // output sites in the tiled walk (walk_zb_for) instead of cb order.
-template <typename LR, typename SR, int NR, int EPI, bool COMP, int TS, bool WALK = false>
+template <typename LR, typename SR, int NR, int EPI, bool COMP, int TS, bool WALK = false, bool PF = false>
 static TuneVariant dslash_variant(hisq_ctx* ctx, const DslashKArgs& a) {
   // the launcher captures two pointers only, so std::function keeps it without a heap allocation
   return TuneVariant{(const void*)dslash_kernel<LR, SR, NR, EPI, COMP, TS>, [ctx, &a](int block) -> cudaError_t {
@@ -56,9 +56,10 @@ static TuneVariant dslash_variant(hisq_ctx* ctx, const DslashKArgs& a) {
                          cap = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
                        }
                        if (grid > cap) grid = cap;
-                       if (WALK) {
+                       if (WALK || PF) {
                          DslashKArgs b = a;
-                         set_walk(ctx, b, walk_zb_for(ctx, NR * TS, 6 * sizeof(SR)));
+                         if (WALK) set_walk(ctx, b, walk_zb_for(ctx, NR * TS, 6 * sizeof(SR)));
+                         b.prefetch = PF ? 1 : 0;
                          dslash_kernel<LR, SR, NR, EPI, COMP, TS><<<grid, block, 0, ctx->stream>>>(b);
                        } else {
                          dslash_kernel<LR, SR, NR, EPI, COMP, TS><<<grid, block, 0, ctx->stream>>>(a);
@@ -107,7 +108,9 @@ static int launch_nr(hisq_ctx* ctx, const DslashKArgs& a, int nr) {
                                  dslash_variant<LR, SR, 2, EPI, COMP, 4>(ctx, a),
                                  dslash_variant<LR, SR, 8, EPI, COMP, 1, true>(ctx, a),
                                  dslash_variant<LR, SR, 4, EPI, COMP, 2, true>(ctx, a),
-                                 dslash_variant<LR, SR, 2, EPI, COMP, 4, true>(ctx, a)};
+                                 dslash_variant<LR, SR, 2, EPI, COMP, 4, true>(ctx, a),
+                                 dslash_variant<LR, SR, 8, EPI, COMP, 1, false, true>(ctx, a),
+                                 dslash_variant<LR, SR, 8, EPI, COMP, 1, true, true>(ctx, a)};
         return launch_tuned(ctx, key, v);
       }
       break;

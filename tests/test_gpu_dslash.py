@@ -222,8 +222,9 @@ def test_slab_loading_matches_whole(hisq):
 
 # launch forms per rhs group (vectors per thread x threads per site), in the tuner's variant order;
 # 8-vector groups exist below FP64 only. Groups of 1 and 8 have each form twice: sites in cb order, and
-# sites in the tiled walk (tiles of z-planes walked along t; on this lattice two tiles of 6 planes).
-FORMS = {1: 2, 2: 2, 4: 3, 8: 6}
+# sites in the tiled walk (tiles of z-planes walked along t; on this lattice two tiles of 6 planes); the
+# 8-vector group's last two forms prefetch each next hop's vectors and link (cb order, tiled walk).
+FORMS = {1: 2, 2: 2, 4: 3, 8: 8}
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
