@@ -111,6 +111,7 @@ def _load():
     lib.hisq_dslash_bytes.argtypes = [vp, ip, ip]
     lib.hisq_dslash_bytes.restype = ctypes.c_double
     lib.hisq_set_autotune.argtypes = [vp, ip]
+    lib.hisq_set_pdl.argtypes = [vp, ip]
     lib.hisq_set_long_compression.argtypes = [vp, dp]
     lib.hisq_launch_count.argtypes = [vp]
     lib.hisq_launch_count.restype = ctypes.c_longlong
@@ -334,6 +335,10 @@ def hisq_launch_count(ctx) -> int:
 
 def hisq_set_autotune(ctx, enable: bool):
     _check(_load().hisq_set_autotune(ctx, int(enable)), "hisq_set_autotune")
+
+
+def hisq_set_pdl(ctx, enable: bool):
+    _check(_load().hisq_set_pdl(ctx, int(enable)), "hisq_set_pdl")
 
 
 def hisq_tune_report(ctx) -> str:

@@ -577,6 +577,13 @@ int hisq_set_autotune(hisq_ctx* c, int enable) {
   return HISQ_OK;
 }
 
+int hisq_set_pdl(hisq_ctx* c, int enable) {
+  if (!c) return set_error(HISQ_EINVAL, "null context");
+  if ((enable ? 1 : 0) != c->pdl) release_graphs(c);  // captured graphs hold the old launch edges
+  c->pdl = enable ? 1 : 0;
+  return HISQ_OK;
+}
+
 int hisq_tune_load(hisq_ctx* c, const char* report, int* loaded) {
   if (!c || !report) return set_error(HISQ_EINVAL, "null argument");
   int n = 0;

@@ -57,7 +57,6 @@ struct DslashKArgs {
   float inv_naik;
   unsigned flags;      // load flags: phases / antiperiodic t (fold signs of compressed links)
   int walk_zb = 0;     // > 0: output sites walked in tiles of walk_zb z-planes (see walk_cb)
-  int prefetch = 0;    // 1 (8-vector forms): each hop requests the next hop's vectors and link ahead
   int walk_chunk = 0;  // walk_zb * Lx Ly / 2: cb numbers per (tile, t) chunk
   unsigned long long walk_m_chunk = 0, walk_m_lt = 0;  // 2^64 / walk_chunk and 2^64 / Lt, rounded up
 };
@@ -83,6 +82,16 @@ struct Comp12 {
   float inv_naik;
   unsigned flags;
 };
+
+// Programmatic dependent launch: a Dslash launched with the programmatic-serialization attribute may
+// be scheduled while the previous launch in the stream drains. griddep_wait returns once every launch
+// it depends on has completed and its writes are visible (at once for a launch without the
+// attribute); nothing of the kernel touches memory before it. griddep_launch_dependents lets the next
+// such launch be scheduled onto the SM slots this grid's blocks free as they finish.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // Requests for data a later hop reads: the vectors into L1, the (streamed, evict-first) link into L2.
 // Hints only: nothing waits on them and no register receives data.
@@ -236,12 +245,16 @@ struct DslashBounds<df64, NR> {
 // (thread sub = threadIdx.x % TS takes vectors sub*NR .. sub*NR+NR-1). The TS lanes of a site sit in
 // one warp and load the same link words in the same instruction, so a link still leaves HBM once
 // per launch, while each thread holds fewer accumulators (more warps in flight per SM).
-template <typename LR, typename SR, int NR, int EPI, bool COMP = false, int TS = 1>
+// PF: the 8-vector forms that prefetch each next hop (a template parameter, so the other forms carry
+// none of its code or registers).
+template <typename LR, typename SR, int NR, int EPI, bool COMP = false, int TS = 1, bool PF = false>
 __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR, NR>::min_blocks)
     dslash_kernel(const DslashKArgs k) {
   using A = typename Real<LR>::acc;  // accumulation type follows the link precision
   using SA = typename Real<SR>::acc;
   static_assert(TS == 1 || TS == 2 || TS == 4, "threads per site");
+  griddep_wait();
+  griddep_launch_dependents();
   if (k.skip && *k.skip) return;  // uniform over the grid
   const Geom& g = k.g;
   const int p = k.out_parity;
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
     const int cb = k.walk_zb ? walk_cb(g, k, w) : w;
     cplx<A> acc[NR][3];
     dslash_site<LR, SR, NR, COMP>(g, k.links, k.blk_bytes, p, cb, in, k.rhs_stride, acc,
-                                  Comp12{k.long12, k.blk12, k.inv_naik, k.flags}, k.prefetch != 0);
+                                  Comp12{k.long12, k.blk12, k.inv_naik, k.flags}, PF);
 
 #pragma unroll
     for (int r = 0; r < NR; ++r) {

@@ -33,12 +33,30 @@ inline void set_walk(const hisq_ctx* ctx, DslashKArgs& a, int zb) {
   a.walk_m_lt = ~0ull / (unsigned long long)ctx->g.L[3] + 1;
 }
 
+// Launches kern<<<grid, block>>>(args) on the context's stream; with ctx->pdl, as a programmatic
+// dependent launch (the kernel starts with griddep_wait, so it may be scheduled while the previous
+// launch drains; in a stream capture this becomes a programmatic edge of the graph).
+template <typename Args>
+static cudaError_t launch_dependent(hisq_ctx* ctx, void (*kern)(Args), int grid, int block, const Args& args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = ctx->pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args);
+}
+
 // One launch form: NR vectors per thread, TS threads per site (NR * TS vectors per launch); WALK: the
 // output sites in the tiled walk (walk_zb_for) instead of cb order.
 template <typename LR, typename SR, int NR, int EPI, bool COMP, int TS, bool WALK = false, bool PF = false>
 static TuneVariant dslash_variant(hisq_ctx* ctx, const DslashKArgs& a) {
   // the launcher captures two pointers only, so std::function keeps it without a heap allocation
-  return TuneVariant{(const void*)dslash_kernel<LR, SR, NR, EPI, COMP, TS>, [ctx, &a](int block) -> cudaError_t {
+  return TuneVariant{(const void*)dslash_kernel<LR, SR, NR, EPI, COMP, TS, PF>, [ctx, &a](int block) -> cudaError_t {
                        int grid = (int)(((size_t)ctx->g.half * TS + block - 1) / block);
                        // Plain launches in cb order: a grid of two resident waves with a grid-stride loop.
                        // The tiled walk's plain launches take one site per thread: blocks are dispatched in
@@ -52,19 +70,13 @@ static TuneVariant dslash_variant(hisq_ctx* ctx, const DslashKArgs& a) {
                        if (EPI == EPI_AXPY && a.partials) {
                          int per_sm = 0;
                          cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                             &per_sm, dslash_kernel<LR, SR, NR, EPI, COMP, TS>, block, 0);
+                             &per_sm, dslash_kernel<LR, SR, NR, EPI, COMP, TS, PF>, block, 0);
                          cap = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
                        }
                        if (grid > cap) grid = cap;
-                       if (WALK || PF) {
-                         DslashKArgs b = a;
-                         if (WALK) set_walk(ctx, b, walk_zb_for(ctx, NR * TS, 6 * sizeof(SR)));
-                         b.prefetch = PF ? 1 : 0;
-                         dslash_kernel<LR, SR, NR, EPI, COMP, TS><<<grid, block, 0, ctx->stream>>>(b);
-                       } else {
-                         dslash_kernel<LR, SR, NR, EPI, COMP, TS><<<grid, block, 0, ctx->stream>>>(a);
-                       }
-                       return cudaGetLastError();
+                       DslashKArgs b = a;
+                       if (WALK) set_walk(ctx, b, walk_zb_for(ctx, NR * TS, 6 * sizeof(SR)));
+                       return launch_dependent(ctx, dslash_kernel<LR, SR, NR, EPI, COMP, TS, PF>, grid, block, b);
                      }};
 }
 

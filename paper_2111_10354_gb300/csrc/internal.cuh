@@ -542,6 +542,7 @@ struct hisq_ctx {
   int num_sms = 0;
   int device = 0;                    // CUDA device current at hisq_create (where the links live)
   int autotune = 1;
+  int pdl = 1;                       // Dslash launches as programmatic dependent launches
   std::map<std::string, DevBuf> ws;  // named device workspaces
   std::map<std::string, int> tune;   // kernel key -> block size
   void* pinned = nullptr;            // small pinned host buffer for scalar read-back
