@@ -579,7 +579,6 @@ int hisq_set_autotune(hisq_ctx* c, int enable) {
 
 int hisq_set_pdl(hisq_ctx* c, int enable) {
   if (!c) return set_error(HISQ_EINVAL, "null context");
-  if ((enable ? 1 : 0) != c->pdl) release_graphs(c);  // captured graphs hold the old launch edges
   c->pdl = enable ? 1 : 0;
   return HISQ_OK;
 }

@@ -167,8 +167,8 @@ def test_programmatic_launch_changes_no_result(hisq, prec):
 
 
 def test_programmatic_launch_solve_bitwise(hisq):
-    """The mixed CG (its iterations replayed as CUDA graphs) returns the same bits with programmatic
-    dependent launch on and off."""
+    """The mixed CG returns the same bits with programmatic dependent launch on and off (its eager launches
+    follow the switch; its captured graphs keep plain launches)."""
     import torch
     L = (8, 8, 8, 8)
     lat, ff, lf = setup(hisq, L)
