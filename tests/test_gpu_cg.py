@@ -38,6 +38,31 @@ def test_cg_8444_plain_method(hisq, inner, rel):
         assert st["reliable_updates"] >= 1
 
 
+@pytest.mark.parametrize("inner", [1, 2])
+def test_cg_every_single_vector_launch_form(hisq, inner):
+    """Mixed CG (FP32 inner vectors, FP32 or FP16 links) with each single-vector Dslash launch form forced
+    for both of its Dslash launches, the fused one reducing <p, Ap> over one resident wave of blocks: cb
+    order and the tiled walk. Each solve is judged by the oracle's true residual; the forms reduce in
+    different orders, so iteration counts may differ by a step or two."""
+    import torch
+    L = (8, 10, 12, 14)
+    dims = "%dx%dx%dx%d" % L
+    its = []
+    for vi in range(2):
+        lat, ff, lf = lattice(hisq, L, 1003, precs=(0, inner))
+        for epi in (0, 1):
+            key = "dslash/l%d/s1/nr1/e%d/c0" % (inner, epi)
+            assert hisq.hisq_tune_load(lat.ctx, "%s %s -> %d\n" % (key, dims, vi * 10000 + 96)) == 1
+        b = hin.gen_source(2003, lat.half, 1)
+        x = torch.zeros((1, lat.half, 3), dtype=torch.complex128, device="cuda")
+        rc, st = lat.cg(x, torch.from_numpy(b).cuda(), 0.05, 1e-10, 4000, inner_prec=inner, reliable_period=50)
+        assert rc == 0 and st["converged"] == 1, vi
+        assert oracle.true_residual(L, ff, lf, 0.05, b[0], x.cpu().numpy()[0]) <= 1e-10, vi
+        its.append(st["iters"])
+        lat.close()
+    assert max(its) - min(its) <= 2, its
+
+
 @pytest.mark.parametrize("inner", [0, 1])
 def test_cg_free_field_exact(hisq, inner):
     import torch
