@@ -48,3 +48,12 @@ def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(h, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         h.hisq_strerror(0)
+
+
+def test_context_switches_reject_a_null_context_without_gpu(libhisq):
+    """The per-context switches validate their context before anything else (no CUDA call is made)."""
+    einval = -1
+    for name in ("hisq_set_autotune", "hisq_set_pdl"):
+        f = getattr(libhisq, name)
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        assert f(None, 1) == einval, name
