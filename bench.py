@@ -428,7 +428,6 @@ def run_ours(args, rank, world, local):
     bytes_launch = lat.dslash_bytes(h.HISQ_F32, 1)
     peak, peak_src = peaks()
     achieved = bytes_launch / (ms_launch * 1e-3) / 1e9
-    launches += 2 * (reps + 3)
 
     # time-to-1e-10 comparisons (mixed FP32, mixed FP16 with FP32 and with FP16 inner vectors, plain FP64)
     # at both masses, and the same with the double-float operator (plain CG, and FP32 inner with
