@@ -86,7 +86,7 @@ def kernel_source_hash():
     """Hash of the code the single-vector Dslash kernel is compiled from (kernel body, its helpers and
     types), comments left out."""
     h = hashlib.sha256()
-    for name in ("dslash_impl.cuh", "internal.cuh", "df64.cuh"):
+    for name in ("dslash_impl.cuh", "internal.cuh", "df64.cuh", "pdl.cuh"):
         with open(os.path.join(ROOT, "paper_2111_10354_gb300", "csrc", name)) as f:
             h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]

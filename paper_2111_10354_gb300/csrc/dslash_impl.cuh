@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "pdl.cuh"
 #include "reduce_warp.cuh"
 
 namespace hisq {
@@ -82,16 +83,6 @@ struct Comp12 {
   float inv_naik;
   unsigned flags;
 };
-
-// Programmatic dependent launch: a Dslash launched with the programmatic-serialization attribute may
-// be scheduled while the previous launch in the stream drains. griddep_wait returns once every launch
-// it depends on has completed and its writes are visible (at once for a launch without the
-// attribute); nothing of the kernel touches memory before it. griddep_launch_dependents lets the next
-// such launch be scheduled onto the SM slots this grid's blocks free as they finish.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // Requests for data a later hop reads: the vectors into L1, the (streamed, evict-first) link into L2.
 // Hints only: nothing waits on them and no register receives data.
@@ -253,7 +244,7 @@ __global__ void __launch_bounds__(DslashBounds<LR, NR>::threads, DslashBounds<LR
   using A = typename Real<LR>::acc;  // accumulation type follows the link precision
   using SA = typename Real<SR>::acc;
   static_assert(TS == 1 || TS == 2 || TS == 4, "threads per site");
-  griddep_wait();
+  griddep_wait();  // a programmatic dependent launch (pdl.cuh): nothing is touched before this
   griddep_launch_dependents();
   if (k.skip && *k.skip) return;  // uniform over the grid
   const Geom& g = k.g;

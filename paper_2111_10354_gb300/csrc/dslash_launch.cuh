@@ -33,26 +33,6 @@ inline void set_walk(const hisq_ctx* ctx, DslashKArgs& a, int zb) {
   a.walk_m_lt = ~0ull / (unsigned long long)ctx->g.L[3] + 1;
 }
 
-// Launches kern<<<grid, block>>>(args) on the context's stream; with ctx->pdl, as a programmatic
-// dependent launch (the kernel starts with griddep_wait, so it may be scheduled while the previous
-// launch drains). Inside the library's own solver captures the launch stays a plain graph node: there
-// the solves gained nothing from programmatic edges (FP32 mixed CG within 0.1%) and the plain FP64 CG
-// lost 2.4%.
-template <typename Args>
-static cudaError_t launch_dependent(hisq_ctx* ctx, void (*kern)(Args), int grid, int block, const Args& args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = ctx->pdl && !ctx->capturing ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, args);
-}
-
 // One launch form: NR vectors per thread, TS threads per site (NR * TS vectors per launch); WALK: the
 // output sites in the tiled walk (walk_zb_for) instead of cb order.
 template <typename LR, typename SR, int NR, int EPI, bool COMP, int TS, bool WALK = false, bool PF = false>

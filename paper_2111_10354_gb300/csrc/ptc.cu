@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "pdl.cuh"
 #include "trace.h"
 #include "tc.cuh"
 
@@ -611,6 +612,8 @@ __device__ __forceinline__ int ptc_hop(const PtcGeom& G, const int c[4], int idx
 __global__ void __launch_bounds__(128, 7) k_ptc_apply_odd(const PtcGeom G, const float2* __restrict__ r,
                                                        __half2* __restrict__ phi, const float2* __restrict__ mix,
                                                        const int* skip) {
+  griddep_wait();  // a programmatic dependent launch (pdl.cuh): nothing is touched before this
+  griddep_launch_dependents();
   if (skip && *skip) return;
   const Geom& g = G.g;
   for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.half; cb += gridDim.x * blockDim.x) {
@@ -662,6 +665,8 @@ __global__ void __launch_bounds__(128, 7) k_ptc_apply_odd(const PtcGeom G, const
 __global__ void __launch_bounds__(256) k_ptc_apply_even(const PtcGeom G, const float2* __restrict__ r,
                                                         const __half2* __restrict__ phi, float2* __restrict__ z,
                                                         const float2* __restrict__ mix, const int* skip) {
+  griddep_wait();  // a programmatic dependent launch (pdl.cuh): nothing is touched before this
+  griddep_launch_dependents();
   if (skip && *skip) return;
   const Geom& g = G.g;
   const float2 m0 = __ldg(mix);
@@ -1088,9 +1093,11 @@ static int network_apply(hisq_ptc* P, float2* z, const float2* r, int nvec, __ha
   // one site per thread (the grid-stride loops then run once); the block scheduler balances the waves
   const int grid_odd = (c->g.half + 127) / 128, grid_even = (c->g.half + 255) / 256;
   for (int v = 0; v < nvec; ++v) {
-    k_ptc_apply_odd<<<grid_odd, 128, 0, c->stream>>>(G, r + v * nh, phi, P->mix, skip);
-    k_ptc_apply_even<<<grid_even, 256, 0, c->stream>>>(G, r + v * nh, phi, z + v * nh, P->mix, skip);
-    HISQ_CUDA(cudaGetLastError());
+    const float2* rv = r + v * nh;
+    float2* zv = z + v * nh;
+    const float2* mix = P->mix;
+    HISQ_CUDA(launch_dependent(c, k_ptc_apply_odd, grid_odd, 128, G, rv, phi, mix, skip));
+    HISQ_CUDA(launch_dependent(c, k_ptc_apply_even, grid_even, 256, G, rv, (const __half2*)phi, zv, mix, skip));
     note_launch(c, 2);
   }
   return HISQ_OK;
