@@ -449,12 +449,12 @@ int hisq_set_autotune(hisq_ctx* ctx, int enable);
 int hisq_tune_report(const hisq_ctx* ctx, char* buf, size_t len);
 int hisq_tune_load(hisq_ctx* ctx, const char* report, int* loaded);
 
-/* Programmatic dependent launch of the Dslash (default on): each single-layout Dslash launch that a
- * call makes on the context's stream (hisq_dslash, hisq_apply_A and their variants, and the eager
- * launches of the solvers) may be scheduled onto the GPU while the launch before it in the stream
- * drains, and waits on the device for that launch's results before it reads or writes anything;
- * results are unchanged. The CUDA graphs the solvers capture keep plain launches. enable = 0 makes
- * every launch a plain stream-ordered one. Errors: HISQ_EINVAL (null context). */
+/* Programmatic dependent launch (default on): each single-layout Dslash launch that a call makes on
+ * the context's stream (hisq_dslash, hisq_apply_A and their variants, and the eager launches of the
+ * solvers), and the two passes of hisq_ptc_apply, may be scheduled onto the GPU while the launch
+ * before it in the stream drains, and wait on the device for that launch's results before they read
+ * or write anything; results are unchanged. The CUDA graphs the solvers capture keep plain launches.
+ * enable = 0 makes every launch a plain stream-ordered one. Errors: HISQ_EINVAL (null context). */
 int hisq_set_pdl(hisq_ctx* ctx, int enable);
 
 /*
