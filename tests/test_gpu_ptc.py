@@ -42,6 +42,29 @@ def test_ptc_forward_parity(setup):
         assert rel(zg[v], ref) <= 1e-2, rel(zg[v], ref)
 
 
+def test_ptc_apply_programmatic_launch_bitwise(setup, hisq):
+    """The network's two passes as programmatic dependent launches give the bits of plain launches, also
+    when applications are chained (each one's input is the previous one's output)."""
+    import torch
+    lat, net, ff, lf = setup
+    W1, W2 = optc.init_weights(17)
+    net.set_weights(W1, W2)
+    r = torch.from_numpy(hin.gen_source(18, lat.half, 1)).to(torch.complex64).cuda()
+    outs = {}
+    for pdl in (1, 0):
+        hisq.hisq_set_pdl(lat.ctx, pdl)
+        zs = [r]
+        for _ in range(3):
+            z = torch.empty_like(r)
+            net.apply(z, zs[-1], 1)
+            zs.append(z)
+        torch.cuda.synchronize()
+        outs[pdl] = [t.clone() for t in zs[1:]]
+    hisq.hisq_set_pdl(lat.ctx, 1)
+    for a, b in zip(outs[1], outs[0]):
+        assert torch.equal(a, b)
+
+
 def test_ptc_identity_network(setup):
     """W1 = W2 = identity hop on channel 0 only: N(r) = r (up to BF16 rounding of r)."""
     import torch
